@@ -1,0 +1,522 @@
+"""FP64 oracle of one NeRF-SLAM mapping step (test infrastructure only).
+
+What it computes, in the paper's order (arXiv 2210.13641, Sec. 3.2 "Mapping:
+Probabilistic Volumetric NeRF", Sec. 3.3 "Architecture", Sec. 3.4 "Implementation
+Details"):
+
+  a1  draw rays uniformly over all keyframes received (Sec. 3.3: the mapping thread
+      optimises all keyframes) and cast them through the pinhole camera;
+  a2  sample 3D positions along each ray (Sec. 3.2, depth rendering) on a uniform
+      grid t_i = t_0 + i*Delta, keep those inside the box and in occupied cells;
+  a3  encode each position with the multiresolution hash grid of Instant-NGP
+      (Sec. 3.4 names it as the map) - trilinear interpolation of per-level tables;
+  a4  encode the view direction with real spherical harmonics, bands 0..3;
+  a5  density MLP, sigma = exp(h_0);  a6  colour MLP with a sigmoid output;
+  a7  alpha compositing of colour and expected depth with the transmittance of
+      Eq. (transmittance) - Sec. 3.2 equations for d* and I*;
+  a8  mapping loss L_M = L_rgb + lambda_D * L_D of Eq. (mapping_loss), colour L2 and
+      the Sigma_D-weighted squared depth residual;
+  a9-a11 the analytic gradient of L_M with respect to the map parameters Theta;
+  a12 Adam on Theta;  a13 occupancy refresh;  a14 forward-only render.
+
+Precision rule: the geometry that decides integers (ray casting, sample positions,
+box and occupancy tests, grid cells) is evaluated in IEEE float32 with a fixed
+operation order, the precision the GPU kernels use, so both sides take every
+integer decision identically.  Everything after that is FP64.
+
+Readings of the paper (where it is silent or defers to Instant-NGP) are listed in
+the repository's design notes; the ones that fix arithmetic here are: Sigma_D is a
+per-pixel variance and the depth residual is divided by it; the colour loss sums
+the three channels; both losses are averaged over rays; delta_i = Delta for every
+sample including the last; samples outside the box or in empty cells are dropped
+(equivalently sigma = 0); background colour 0.
+
+Parity status: every function below is pinned by the not-gpu tests (closed forms,
+invariants, brute force, finite differences) except the SplitMix64 constants and
+the hash primes, which are taken from their published definitions and can only be
+checked structurally ("parity unpinned" for those constants).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+f32 = np.float32
+U64 = np.uint64
+MASK32 = 0xFFFFFFFF
+
+# ------------------------------------------------------------------ a1: counter RNG
+
+# SplitMix64 (Steele, Lea & Flood, OOPSLA 2014; the output function as published in
+# Vigna's splitmix64.c): state advances by the golden gamma, then two xor-shift /
+# odd-multiply rounds.  Used as a counter-based generator: output = mix(seed ^ ctr).
+SM_GAMMA = 0x9E3779B97F4A7C15
+SM_M1 = 0xBF58476D1CE4E5B9
+SM_M2 = 0x94D049BB133111EB
+OCC_STREAM = 1 << 30
+
+
+def splitmix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 output for state z (uint64 array), wrap-around arithmetic."""
+    z = np.asarray(z, dtype=U64)
+    with np.errstate(over="ignore"):
+        z = z + U64(SM_GAMMA)
+        z = (z ^ (z >> U64(30))) * U64(SM_M1)
+        z = (z ^ (z >> U64(27))) * U64(SM_M2)
+    return z ^ (z >> U64(31))
+
+
+def counter_rand(seed: int, stream: int, index: np.ndarray, k: int) -> np.ndarray:
+    """u64 random number for (seed, stream, index, k): counter = stream<<33 | index<<1 | k."""
+    index = np.asarray(index, dtype=U64)
+    ctr = (U64(stream) << U64(33)) | (index << U64(1)) | U64(k)
+    return splitmix64(U64(seed) ^ ctr)
+
+
+def draw_rays(seed: int, step: int, n_rays: int, kf_sizes):
+    """Uniform draw with replacement over (keyframe, pixel), Sec. 3.3 (all keyframes
+    are optimised).  kf_sizes = [(W, H), ...] in insertion order.  Returns keyframe
+    index, u, v (int64 arrays)."""
+    r = np.arange(n_rays, dtype=U64)
+    n_kf = len(kf_sizes)
+    r0 = counter_rand(seed, step, r, 0)
+    r1 = counter_rand(seed, step, r, 1)
+    kf = (r0 % U64(n_kf)).astype(np.int64)
+    Ws = np.array([s[0] for s in kf_sizes], dtype=U64)
+    Hs = np.array([s[1] for s in kf_sizes], dtype=U64)
+    pix = r1 % (Ws[kf] * Hs[kf])
+    u = (pix % Ws[kf]).astype(np.int64)
+    v = (pix // Ws[kf]).astype(np.int64)
+    return kf, u, v
+
+
+def cast_rays_f32(c2w: np.ndarray, K: np.ndarray, u: np.ndarray, v: np.ndarray):
+    """Pinhole back-projection Pi^-1 of the pixel centre (u+1/2, v+1/2) (Sec. 3.1
+    projection model), rotated to world and normalised; float32, fixed op order.
+    c2w [N,3,4], K [N,4] -> origin o [N,3], unit direction d [N,3] (float32)."""
+    c2w = c2w.astype(f32)
+    K = K.astype(f32)
+    dx = ((u.astype(f32) + f32(0.5)) - K[:, 2]) / K[:, 0]
+    dy = ((v.astype(f32) + f32(0.5)) - K[:, 3]) / K[:, 1]
+    R = c2w[:, :, :3]
+    w = [(R[:, a, 0] * dx + R[:, a, 1] * dy) + R[:, a, 2] for a in range(3)]
+    n = np.sqrt((w[0] * w[0] + w[1] * w[1]) + w[2] * w[2])
+    d = np.stack([w[0] / n, w[1] / n, w[2] / n], axis=1)
+    o = c2w[:, :, 3].copy()
+    return o, d
+
+
+def ray_targets(kf, u, v, keyframes):
+    """Targets I (3), D, Sigma_D of each drawn ray in ray-distance units (FP64).
+
+    A z-depth D_z of pixel (u,v) lies at distance D_z * ||K^-1 [u+1/2, v+1/2, 1]||
+    along the unit ray, and its variance scales with the square of that factor."""
+    n = len(kf)
+    I = np.zeros((n, 3))
+    D = np.zeros(n)
+    V = np.zeros(n)
+    for j, k in enumerate(keyframes):
+        m = kf == j
+        if not np.any(m):
+            continue
+        uu, vv = u[m], v[m]
+        I[m] = k.rgb[vv, uu].astype(np.float64)
+        z = k.depth[vv, uu].astype(np.float64)
+        var = k.var[vv, uu].astype(np.float64)
+        if k.depth_is_z:
+            fx, fy, cx, cy = [float(a) for a in k.K]
+            sx = (uu + 0.5 - cx) / fx
+            sy = (vv + 0.5 - cy) / fy
+            s = np.sqrt(sx * sx + sy * sy + 1.0)
+            D[m] = z * s
+            V[m] = var * s * s
+        else:
+            D[m] = z
+            V[m] = var
+    return I, D, V
+
+
+# ------------------------------------------------------------------ a2: march
+
+def occupancy_bit(bits: np.ndarray, res: int, x: np.ndarray) -> np.ndarray:
+    """Bit of the occupancy cell holding grid position x [N,3] (float32).
+    Cell c_a = min(floor(x_a * res), res-1); linear index cx + res*(cy + res*cz);
+    bit (b & 7) of byte (b >> 3)."""
+    q = x * f32(res)
+    c = np.minimum(np.floor(q).astype(np.int64), res - 1)
+    c = np.maximum(c, 0)
+    b = c[:, 0] + res * (c[:, 1] + res * c[:, 2])
+    return ((bits[b >> 3] >> (b & 7).astype(np.uint8)) & 1).astype(bool)
+
+
+def sample_positions_f32(cfg, o, d, i):
+    """t_i = t_0 + i*Delta and the grid position x = (o + t d - origin) * inv_size,
+    float32 with this exact operation order.  i: int array broadcast against rays."""
+    t = f32(cfg.near) + i.astype(f32) * f32(cfg.step)
+    p = o[..., None, :] + t[..., None] * d[..., None, :]
+    x = (p - cfg.grid_origin.astype(f32)) * f32(cfg.grid_inv_size)
+    return t, x
+
+
+def march(cfg, o, d, occ_bits=None):
+    """Sec. 3.2: sample positions along each ray.  Steps i = 0..n_steps-1; a step is
+    kept when 0 <= x_a < box_a on every axis and (with a bitfield) its cell is
+    occupied; the first max_samples kept steps of each ray are its samples.
+    Returns ray id [S], step index [S], t [S] (float32), x [S,3] (float32), all in
+    ray-major order."""
+    n = o.shape[0]
+    i = np.arange(cfg.n_steps)
+    t, x = sample_positions_f32(cfg, o, d, np.broadcast_to(i, (n, cfg.n_steps)))
+    box = cfg.box_max.astype(f32)
+    keep = np.all((x >= f32(0)) & (x < box), axis=-1)
+    if occ_bits is not None and cfg.occ_res > 0:
+        flat = x.reshape(-1, 3)
+        occ = np.zeros(flat.shape[0], bool)
+        kf = keep.reshape(-1)
+        occ[kf] = occupancy_bit(occ_bits, cfg.occ_res, flat[kf])
+        keep &= occ.reshape(keep.shape)
+    rank = np.cumsum(keep, axis=1) - 1
+    keep &= rank < cfg.max_samples
+    ray_id, step_idx = np.nonzero(keep)
+    return ray_id, step_idx, t[ray_id, step_idx], x[ray_id, step_idx]
+
+
+# ------------------------------------------------------------------ a3: hash grid
+
+PI1, PI2, PI3 = 1, 2654435761, 805459861   # spatial-hash primes of Instant-NGP
+
+
+def level_resolutions(cfg) -> list:
+    """N_l = floor(N_min * b^l), b = growth or exp(ln(N_max/N_min)/(L-1)).  A 1e-9
+    relative nudge keeps exactly-integral products (16 * 2^(7*15/15) = 2048) from
+    flooring one below through FP64 rounding."""
+    L = cfg.n_levels
+    if cfg.growth is not None:
+        b = float(cfg.growth)
+    else:
+        b = math.exp(math.log(cfg.n_max / cfg.n_min) / (L - 1))
+    return [int(math.floor(cfg.n_min * b ** l * (1 + 1e-9))) for l in range(L)]
+
+
+def vertex_index(c: np.ndarray, N: int, T: int) -> np.ndarray:
+    """Table slot of integer grid vertices c [...,3] at resolution N (coords 0..N).
+    Dense when the (N+1)^3 vertices fit in T slots: cx + cy(N+1) + cz(N+1)^2;
+    otherwise the spatial hash (cx*pi1 xor cy*pi2 xor cz*pi3) mod 2^32 mod T."""
+    c = c.astype(np.int64)
+    if (N + 1) ** 3 <= T:
+        return c[..., 0] + (N + 1) * (c[..., 1] + (N + 1) * c[..., 2])
+    h = ((c[..., 0] * PI1) & MASK32) ^ ((c[..., 1] * PI2) & MASK32) ^ ((c[..., 2] * PI3) & MASK32)
+    return (h & MASK32) % T
+
+
+CORNERS = np.array([[(k >> 0) & 1, (k >> 1) & 1, (k >> 2) & 1] for k in range(8)])
+
+
+def grid_cell_f32(x: np.ndarray, N: int):
+    """Cell and fractional offset of x [S,3] at resolution N: q = x*N (float32),
+    c = min(floor(q), N-1), w = q - c (exact).  Returns c int64 [S,3], w FP64 [S,3]."""
+    q = x.astype(f32) * f32(N)
+    c = np.minimum(np.floor(q).astype(np.int64), N - 1)
+    w = q.astype(np.float64) - c
+    return c, w
+
+
+def hash_encode(cfg, level_res, tables: np.ndarray, x: np.ndarray):
+    """Multiresolution grid encoding (Instant-NGP, the map named in Sec. 3.4).
+    x [S,3] float32 in [0,1).  Returns features [S, enc_width] (FP64, zero padded
+    beyond L*F), slot indices [S, L, 8] and trilinear weights [S, L, 8]."""
+    S = x.shape[0]
+    L, F, T = cfg.n_levels, cfg.n_features, cfg.table_size
+    feat = np.zeros((S, cfg.enc_width))
+    idx = np.zeros((S, L, 8), dtype=np.int64)
+    wts = np.zeros((S, L, 8))
+    tab = tables.astype(np.float64)
+    for l in range(L):
+        N = level_res[l]
+        c, w = grid_cell_f32(x, N)
+        for k in range(8):
+            b = CORNERS[k]
+            wk = np.prod(np.where(b[None, :] == 1, w, 1.0 - w), axis=1)
+            ik = vertex_index(c + b[None, :], N, T)
+            idx[:, l, k] = ik
+            wts[:, l, k] = wk
+            feat[:, l * F:(l + 1) * F] += wk[:, None] * tab[l, ik]
+    return feat, idx, wts
+
+
+# ------------------------------------------------------------------ a4: SH
+
+def sh_deg4(d: np.ndarray) -> np.ndarray:
+    """Real spherical harmonics Y_l^m, l = 0..3 (16 values), of unit directions d
+    [S,3]; orthonormal on the sphere, Condon-Shortley phase.  Each constant is the
+    normalisation sqrt((2l+1)/(4 pi) * (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0)
+    of the associated Legendre closed form."""
+    x, y, z = d[:, 0].astype(np.float64), d[:, 1].astype(np.float64), d[:, 2].astype(np.float64)
+    pi = math.pi
+    out = np.empty((d.shape[0], 16))
+    out[:, 0] = 0.5 * math.sqrt(1 / pi)
+    a1 = math.sqrt(3 / (4 * pi))
+    out[:, 1] = -a1 * y
+    out[:, 2] = a1 * z
+    out[:, 3] = -a1 * x
+    out[:, 4] = 0.5 * math.sqrt(15 / pi) * x * y
+    out[:, 5] = -0.5 * math.sqrt(15 / pi) * y * z
+    out[:, 6] = 0.25 * math.sqrt(5 / pi) * (3 * z * z - 1)
+    out[:, 7] = -0.5 * math.sqrt(15 / pi) * x * z
+    out[:, 8] = 0.25 * math.sqrt(15 / pi) * (x * x - y * y)
+    out[:, 9] = -0.25 * math.sqrt(35 / (2 * pi)) * y * (3 * x * x - y * y)
+    out[:, 10] = 0.5 * math.sqrt(105 / pi) * x * y * z
+    out[:, 11] = -0.25 * math.sqrt(21 / (2 * pi)) * y * (5 * z * z - 1)
+    out[:, 12] = 0.25 * math.sqrt(7 / pi) * z * (5 * z * z - 3)
+    out[:, 13] = -0.25 * math.sqrt(21 / (2 * pi)) * x * (5 * z * z - 1)
+    out[:, 14] = 0.25 * math.sqrt(105 / pi) * z * (x * x - y * y)
+    out[:, 15] = -0.25 * math.sqrt(35 / (2 * pi)) * x * (x * x - 3 * y * y)
+    return out
+
+
+# ------------------------------------------------------------------ a5, a6: MLPs
+
+def relu(a):
+    return np.maximum(a, 0.0)
+
+
+def field_forward(P: dict, feat: np.ndarray, sh: np.ndarray) -> dict:
+    """sigma_i and c_i from one evaluation of the MLPs at the sample (Sec. 3.2: both
+    are estimated simultaneously).  Density MLP: h = W2 relu(W1 feat), sigma =
+    exp(h_0).  Colour MLP on [h; SH]: c = sigmoid(W5 relu(W4 relu(W3 [h; SH]))).
+    No biases.  Returns every intermediate (for the backward pass)."""
+    W = {k: P[k].astype(np.float64) for k in ("W1", "W2", "W3", "W4", "W5")}
+    a1 = feat @ W["W1"].T
+    h1 = relu(a1)
+    h = h1 @ W["W2"].T
+    sigma = np.exp(h[:, 0])
+    x3 = np.concatenate([h, sh], axis=1)
+    a3 = x3 @ W["W3"].T
+    h3 = relu(a3)
+    a4 = h3 @ W["W4"].T
+    h4 = relu(a4)
+    z = h4 @ W["W5"].T
+    rgb = 1.0 / (1.0 + np.exp(-z))
+    return dict(feat=feat, a1=a1, h1=h1, h=h, sigma=sigma, x3=x3, a3=a3, h3=h3,
+                a4=a4, h4=h4, z=z, rgb=rgb)
+
+
+# ------------------------------------------------------------------ a7: compositing
+
+def composite_ray(sigma, rgb, t, delta, t_min=None):
+    """Sec. 3.2 for one ray: alpha_i = 1 - exp(-sigma_i delta), transmittance
+    T_i = exp(-sum_{j<i} sigma_j delta) (Eq. transmittance), weight w_i = T_i alpha_i,
+    I* = sum w_i c_i, d* = sum w_i t_i, acc = sum w_i.  With t_min (render only) the
+    sum stops at the first sample whose T_i < t_min."""
+    tau = sigma * delta
+    Tcum = np.exp(-np.concatenate([[0.0], np.cumsum(tau)[:-1]]))
+    alpha = -np.expm1(-tau)
+    w = Tcum * alpha
+    if t_min is not None:
+        w = np.where(Tcum < t_min, 0.0, w)
+        # once below t_min the ray stays terminated (T is non-increasing)
+    I = (w[:, None] * rgb).sum(0) if len(w) else np.zeros(3)
+    D = float((w * t).sum())
+    return I, D, float(w.sum()), w, Tcum
+
+
+def composite(ray_id, sigma, rgb, t, delta, n_rays, t_min=None):
+    """composite_ray over every ray (rays with no samples render 0)."""
+    I = np.zeros((n_rays, 3))
+    D = np.zeros(n_rays)
+    A = np.zeros(n_rays)
+    w_all = np.zeros(len(sigma))
+    T_all = np.zeros(len(sigma))
+    starts = np.searchsorted(ray_id, np.arange(n_rays + 1))
+    for r in range(n_rays):
+        a, b = starts[r], starts[r + 1]
+        if a == b:
+            continue
+        I[r], D[r], A[r], w_all[a:b], T_all[a:b] = composite_ray(
+            sigma[a:b], rgb[a:b], t[a:b], delta, t_min)
+    return I, D, A, w_all, T_all
+
+
+# ------------------------------------------------------------------ a8: loss
+
+def mapping_loss(I_hat, D_hat, I, D, V, lambda_d):
+    """Eq. (mapping_loss): L_M = L_rgb + lambda_D L_D with L_rgb = ||I - I*||^2
+    (summed over channels) and L_D = ||D - D*||^2_{Sigma_D} = (D - D*)^2 / Sigma_D,
+    both averaged over the rays of the batch.  Returns (L_M, per-ray terms)."""
+    lrgb = ((I - I_hat) ** 2).sum(1)
+    ld = (D - D_hat) ** 2 / V
+    per_ray = lrgb + lambda_d * ld
+    return float(per_ray.mean()), per_ray
+
+
+# ------------------------------------------------------------------ a9: composite bwd
+
+def composite_backward_ray(sigma, rgb, t, delta, w, Tcum, gI, gD):
+    """Gradient of g_I . I* + g_D d* for one ray with respect to sigma_i and c_i.
+    dI*/dc_i = w_i; dI*/dsigma_i = delta (T_{i+1} c_i - sum_{j>i} w_j c_j), and the
+    same for d* with t_i in place of c_i (from the compositing of Sec. 3.2)."""
+    T_next = Tcum * np.exp(-sigma * delta)
+    wc = w[:, None] * rgb
+    wt = w * t
+    suf_c = np.cumsum(wc[::-1], axis=0)[::-1] - wc      # sum_{j>i}
+    suf_t = np.cumsum(wt[::-1])[::-1] - wt
+    dsig = delta * ((T_next[:, None] * rgb - suf_c) @ gI + gD * (T_next * t - suf_t))
+    drgb = w[:, None] * gI[None, :]
+    return dsig, drgb
+
+
+# ------------------------------------------------------------------ a10, a11: backward
+
+def field_backward(P: dict, fw: dict, dsigma, drgb):
+    """Chain rule through the MLPs (a10).  Returns weight gradients and dL/dfeat."""
+    W = {k: P[k].astype(np.float64) for k in ("W1", "W2", "W3", "W4", "W5")}
+    rgb = fw["rgb"]
+    dz = drgb * rgb * (1.0 - rgb)
+    g = {"W5": dz.T @ fw["h4"]}
+    dh4 = dz @ W["W5"]
+    da4 = dh4 * (fw["a4"] > 0)
+    g["W4"] = da4.T @ fw["h3"]
+    dh3 = da4 @ W["W4"]
+    da3 = dh3 * (fw["a3"] > 0)
+    g["W3"] = da3.T @ fw["x3"]
+    dx3 = da3 @ W["W3"]
+    dh = dx3[:, :P["W2"].shape[0]].copy()
+    dh[:, 0] += dsigma * fw["sigma"]
+    g["W2"] = dh.T @ fw["h1"]
+    dh1 = dh @ W["W2"]
+    da1 = dh1 * (fw["a1"] > 0)
+    g["W1"] = da1.T @ fw["feat"]
+    dfeat = da1 @ W["W1"]
+    return g, dfeat
+
+
+def hash_backward(cfg, idx, wts, dfeat):
+    """a11: dL/dtable[l, idx_k] += w_k * dL/dfeat_l for every corner and level."""
+    L, F, T = cfg.n_levels, cfg.n_features, cfg.table_size
+    g = np.zeros((L, T, F))
+    for l in range(L):
+        for f in range(F):
+            np.add.at(g[l, :, f], idx[:, l, :].ravel(),
+                      (wts[:, l, :] * dfeat[:, l * F + f][:, None]).ravel())
+    return g
+
+
+# ------------------------------------------------------------------ the step
+
+def forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits=None,
+                     level_res=None, rays=None, want_grad=True):
+    """a1-a11: loss L_M and its gradient for one batch.  Returns a dict with the
+    loss, per-ray renders, the sample list and the named gradients."""
+    level_res = level_resolutions(cfg) if level_res is None else level_res
+    if rays is None:
+        kf, u, v = draw_rays(seed, step, n_rays, [(k.W, k.H) for k in keyframes])
+    else:
+        kf, u, v = rays
+    c2w = np.stack([keyframes[j].c2w for j in kf]) if n_rays else np.zeros((0, 3, 4), f32)
+    K = np.stack([keyframes[j].K for j in kf]) if n_rays else np.zeros((0, 4), f32)
+    o, d = cast_rays_f32(c2w, K, u, v)
+    I, D, V = ray_targets(kf, u, v, keyframes)
+    ray_id, step_idx, t, x = march(cfg, o, d, occ_bits)
+    feat, idx, wts = hash_encode(cfg, level_res, P["tables"], x)
+    sh = sh_deg4(d[ray_id])
+    fw = field_forward(P, feat, sh)
+    delta = float(cfg.step)
+    t64 = t.astype(np.float64)
+    I_hat, D_hat, acc, w, Tcum = composite(ray_id, fw["sigma"], fw["rgb"], t64, delta, n_rays)
+    lam = float(cfg.lambda_d)
+    loss, per_ray = mapping_loss(I_hat, D_hat, I, D, V, lam)
+    out = dict(loss=loss, per_ray=per_ray, I_hat=I_hat, D_hat=D_hat, acc=acc, kf=kf, u=u,
+               v=v, o=o, d=d, I=I, D=D, V=V, ray_id=ray_id, step_idx=step_idx, t=t, x=x,
+               sigma=fw["sigma"], rgb=fw["rgb"], w=w, level_res=level_res)
+    if not want_grad:
+        return out
+    gI = -2.0 * (I - I_hat) / n_rays
+    gD = -2.0 * lam * (D - D_hat) / (V * n_rays)
+    dsig = np.zeros(len(t))
+    drgb = np.zeros((len(t), 3))
+    starts = np.searchsorted(ray_id, np.arange(n_rays + 1))
+    for r in range(n_rays):
+        a, b = starts[r], starts[r + 1]
+        if a == b:
+            continue
+        dsig[a:b], drgb[a:b] = composite_backward_ray(
+            fw["sigma"][a:b], fw["rgb"][a:b], t64[a:b], delta, w[a:b], Tcum[a:b], gI[r], gD[r])
+    g, dfeat = field_backward(P, fw, dsig, drgb)
+    g["tables"] = hash_backward(cfg, idx, wts, dfeat)
+    out.update(grads=g, dsigma=dsig, drgb=drgb, dfeat=dfeat)
+    return out
+
+
+def loss_only(cfg, P, keyframes, n_rays, seed, step, occ_bits=None, level_res=None, rays=None):
+    return forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits, level_res,
+                            rays, want_grad=False)["loss"]
+
+
+# ------------------------------------------------------------------ a12: Adam
+
+def adam_update(P: dict, G: dict, M: dict, Vm: dict, t: int, cfg):
+    """Adam (Kingma & Ba 2015) with bias correction, dense over all parameters:
+    m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;  p -= lr * m_hat / (sqrt(v_hat) + eps),
+    m_hat = m / (1 - b1^t), v_hat = v / (1 - b2^t).  t counts from 1.  FP64."""
+    lr, b1, b2, eps = (float(cfg.lr), float(cfg.beta1), float(cfg.beta2), float(cfg.eps))
+    newP, newM, newV = {}, {}, {}
+    for k in P:
+        g = G[k].astype(np.float64)
+        m = b1 * M[k] + (1 - b1) * g
+        v = b2 * Vm[k] + (1 - b2) * g * g
+        mh = m / (1 - b1 ** t)
+        vh = v / (1 - b2 ** t)
+        newP[k] = P[k].astype(np.float64) - lr * mh / (np.sqrt(vh) + eps)
+        newM[k], newV[k] = m, v
+    return newP, newM, newV
+
+
+# ------------------------------------------------------------------ a13: occupancy
+
+def occupancy_refresh(cfg, P, density, refresh_idx, seed, level_res=None):
+    """Cell density EMA: d <- max(decay * d, sigma(x_cell)) at one seeded point per
+    cell, then bit = d > threshold.  x_cell = (c + u) / res per axis, u from three
+    21-bit fields of one counter draw (stream OCC_STREAM + refresh_idx, index = cell).
+    Returns (new density FP64 [res^3], packed bits uint8, positions [res^3, 3])."""
+    level_res = level_resolutions(cfg) if level_res is None else level_res
+    res = cfg.occ_res
+    n = res ** 3
+    cell = np.arange(n, dtype=np.int64)
+    r = counter_rand(seed, OCC_STREAM + refresh_idx, cell.astype(U64), 0)
+    u = np.stack([((r >> U64(21 * a)) & U64(0x1FFFFF)).astype(np.float64) for a in range(3)], 1)
+    u = (u * 2.0 ** -21).astype(f32)          # exact: 21-bit fractions
+    c = np.stack([cell % res, (cell // res) % res, cell // (res * res)], 1).astype(f32)
+    x = (c + u) / f32(res)
+    feat, _, _ = hash_encode(cfg, level_res, P["tables"], x)
+    W1 = P["W1"].astype(np.float64)
+    W2 = P["W2"].astype(np.float64)
+    sig = np.exp((relu(feat @ W1.T) @ W2.T)[:, 0])
+    newd = np.maximum(float(cfg.occ_decay) * density, sig)
+    bits = np.packbits(newd > float(cfg.occ_thresh), bitorder="little")
+    return newd, bits, x
+
+
+# ------------------------------------------------------------------ a14: render
+
+def render_rays_f32(c2w, K, W, H):
+    """All pixel rays of one view, row-major (v outer, u inner)."""
+    v, u = np.divmod(np.arange(W * H, dtype=np.int64), W)
+    n = W * H
+    o, d = cast_rays_f32(np.broadcast_to(c2w, (n, 3, 4)), np.broadcast_to(K, (n, 4)), u, v)
+    return o, d
+
+
+def render(cfg, P, c2w, K, W, H, occ_bits=None, level_res=None, t_min=None):
+    """Forward-only render of a W x H view (PAPER Sec. 3.3, the mapping thread also
+    renders): colour [H*W, 3] and expected depth [H*W]; with t_min, samples after
+    the transmittance drops below t_min are skipped."""
+    level_res = level_resolutions(cfg) if level_res is None else level_res
+    o, d = render_rays_f32(np.asarray(c2w, f32), np.asarray(K, f32), W, H)
+    ray_id, _, t, x = march(cfg, o, d, occ_bits)
+    feat, _, _ = hash_encode(cfg, level_res, P["tables"], x)
+    fw = field_forward(P, feat, sh_deg4(d[ray_id]))
+    I_hat, D_hat, acc, _, _ = composite(ray_id, fw["sigma"], fw["rgb"], t.astype(np.float64),
+                                        float(cfg.step), W * H, t_min)
+    return I_hat, D_hat, acc
