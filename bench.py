@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Mapping-step benchmark: rays/s of one fwd+bwd+Adam mapping step on the room
+workload (L=16, F=2, T=2^19, N 16..2048, 128^3 occupancy bitfield, 2^18 rays per
+batch drawn from 20 keyframes of 640x480), plus render Mpx/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16|bf16]
+  python bench.py --impl reference ...   # the FP64 oracle on the host cores
+
+Prints one JSON line on rank 0.  With N > 1 (torchrun) every rank runs an
+independent replica of the workload (no collective on the data path; one barrier
+and a max-reduction of the timings), so scaling is weak.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_RAYS = 1 << 18
+N_KF = 20
+METRIC = "mapping rays/s (fwd+bwd+Adam)"
+UNIT = "rays/s"
+WORKLOAD = ("room 6x4x3 m, 30 primitives, 20 keyframes 640x480 (fx=fy=525), L=16 F=2 T=2^19 "
+            "N_min=16 N_max=2048, 128^3 occupancy bitfield from the analytic surfaces, "
+            "2^18 rays/step, <=128 samples/ray (Delta=|diag|/1024)")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    p.add_argument("--rays", type=int, default=N_RAYS)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--sample-rays", type=int, default=2048, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+def make_workload(precision: str, seed: int = 0):
+    import synth
+    cfg = synth.config_c2(precision=precision)
+    room = synth.make_room(seed)
+    kfs = synth.room_keyframes(room, N_KF, seed=seed + 1)
+    bits = synth.room_occupancy_bits(room, cfg.occ_res, cfg.grid_origin, cfg.grid_inv_size)
+    params = synth.random_params(cfg, seed)
+    return cfg, kfs, bits, params
+
+
+# ----------------------------------------------------------------- oracle (CPU) arm
+
+def oracle_steps(cfg, kfs, bits, params, n_sample, n_steps, seed=0):
+    """Oracle fwd+bwd on `n_sample` rays of the workload plus Adam over all
+    parameters, `n_steps` times; returns seconds per step."""
+    import numpy as np
+    import oracle
+    P = {k: v.astype(np.float64) for k, v in params.items()}
+    M = {k: np.zeros_like(v) for k, v in P.items()}
+    V = {k: np.zeros_like(v) for k, v in P.items()}
+    times = []
+    for s in range(n_steps):
+        t0 = time.perf_counter()
+        out = oracle.forward_backward(cfg, P, kfs, n_sample, seed, s, occ_bits=bits)
+        P, M, V = oracle.adam_update(P, out["grads"], M, V, s + 1, cfg)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_baseline_child(args):
+    cfg, kfs, bits, params = make_workload("fp32")
+    times = oracle_steps(cfg, kfs, bits, params, args.sample_rays, 1)
+    print(json.dumps({"value": args.sample_rays / times[0], "seconds": times[0]}))
+
+
+def run_cpu_baseline(sample_rays: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only",
+                        "--sample-rays", str(sample_rays)], env=env, capture_output=True, text=True,
+                       timeout=900)
+    if p.returncode != 0:
+        return {"error": p.stderr.strip().splitlines()[-1] if p.stderr.strip() else "failed"}
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    return {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample_rays} rays of the workload, one fwd+bwd+Adam step in FP64 numpy "
+                      f"({r['seconds']:.1f} s; Adam over all parameters)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg, kfs, bits, params = make_workload("fp32")
+    n = args.sample_rays
+    oracle_steps(cfg, kfs, bits, params, n, args.warmup)
+    times = oracle_steps(cfg, kfs, bits, params, n, args.steps)
+    tot = sum(times)
+    value = n * args.steps / tot
+    cores = 1 if os.environ.get("OPENBLAS_NUM_THREADS") == "1" else os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "rays_per_step": n,
+                                            "note": "FP64 CPU oracle, bounded sample of each step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} rays per step of the workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.rows = []
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if bus_id:
+            cmd += ["-i", bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- our arm
+
+def algorithmic_bytes(cfg, n_samples, n_params):
+    """Algorithmic bytes per launch of the field kernels and Adam."""
+    L, F = cfg.n_levels, cfg.n_features
+    table = 8 * L * F * 4                 # 8 corners x L levels x F FP32 features
+    per_sample_io = 8 + 128 + 16          # (ray, t), stored encoding, (sigma, rgb) / their grads
+    return {"field_fwd": n_samples * (table + per_sample_io),
+            "field_bwd": n_samples * (table + per_sample_io),
+            "adam": 32 * n_params}
+
+
+def main():
+    args = parse()
+    if args.cpu_baseline_only:
+        cpu_baseline_child(args)
+        return
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(args.sample_rays)       # before any CUDA work in this process
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2210_13641_gb300 import NerfMap, pack_params
+
+    cfg, kfs, bits, params = make_workload(args.precision)
+    m = NerfMap(cfg, occ_every=0)
+    m.set_params(pack_params(params))
+    m.set_occupancy(bits)
+    for kf in kfs:
+        m.add_keyframe(kf)
+    stream = torch.cuda.current_stream()
+    n = args.rays
+    for i in range(args.warmup):
+        m.step(n, seed=1000 + i, want_loss=False, stream=stream)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K device-resident steps
+    props = torch.cuda.get_device_properties(local)
+    bus = getattr(props, "pci_bus_id", None)
+    clocks = ClockSampler(bus)
+    time.sleep(0.3)
+    launches0 = m.stats().kernel_launches
+    m.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        m.step(n, seed=2000 + i, want_loss=False, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = m.profile_read()
+    m.profile(False)
+    launches = m.stats().kernel_launches - launches0
+    n_samples = m.stats().n_samples
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = n * args.steps * world / (ms / 1e3)
+
+    # ---------------- roofline of the dominant kernel (phase times inside the timed region)
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ab = algorithmic_bytes(cfg, n_samples, m.n_params)
+    cand = {k: prof[k]["ms"] / max(prof[k]["count"], 1) for k in ("field_fwd", "field_bwd", "adam")}
+    dom = max(cand, key=cand.get)
+    achieved = ab[dom] / (cand[dom] / 1e3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "phase_ms_per_step": {k: v["ms"] / max(v["count"], 1) for k, v in prof.items() if v["count"]}}
+
+    # ---------------- end to end: keyframe upload from pinned host memory + step + loss read
+    pinned = []
+    for kf in kfs[:4]:
+        rgb = torch.from_numpy(kf.rgb).pin_memory()
+        dep = torch.from_numpy(kf.depth).pin_memory()
+        var = torch.from_numpy(kf.var).pin_memory()
+        pinned.append((kf, rgb.numpy(), dep.numpy(), var.numpy()))
+    h2d = pinned[0][1].nbytes + pinned[0][2].nbytes + pinned[0][3].nbytes + 64
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        kf, rgb, dep, var = pinned[i % len(pinned)]
+        m.add_keyframe(kf, rgb=rgb, depth=dep, var=var, stream=stream)
+        m.step(n, seed=3000 + i, want_loss=True, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": n * args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": 4}
+
+    # ---------------- render Mpx/s (640x480 views, device output buffers)
+    W, H = 640, 480
+    out = torch.empty((H, W, 3), device="cuda")
+    dep = torch.empty((H, W), device="cuda")
+    for i in range(3):
+        m.render(kfs[i].c2w, kfs[i].K, W, H, out_rgb=out, out_depth=dep, stream=stream)
+    torch.cuda.synchronize()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    nv = max(args.steps, 5)
+    for i in range(nv):
+        k = kfs[i % len(kfs)]
+        m.render(k.c2w, k.K, W, H, out_rgb=out, out_depth=dep, stream=stream)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    render_mpx = W * H * nv / (r0.elapsed_time(r1) / 1e3) / 1e6 * world
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16+f32",
+                                                                "bf16": "bf16+f32"}[args.precision],
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "rays_per_step": n, "mlp_precision": args.precision,
+                           "samples_per_step": n_samples, "mean_samples_per_ray": n_samples / n,
+                           "l2": "working set > L2: params+grads+Adam moments (0.27 GB) streamed every step",
+                           "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+                "roofline": roof, "render_mpx_s": render_mpx, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(launches)}
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    m.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

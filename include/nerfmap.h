@@ -1,0 +1,254 @@
+/*
+ * nerfmap.h - C ABI of the GB300 mapping library (NeRF-SLAM mapping stage,
+ * arXiv 2210.13641).
+ *
+ * The library fits a multiresolution hash-grid radiance field to posed keyframes
+ * that carry colour, dense depth and a per-pixel depth variance, by minimising the
+ * mapping loss L_M = L_rgb + lambda_D * L_D of the paper's Eq. (mapping_loss)
+ * (Sec. 3.2), and renders views of the fitted field (Sec. 3.3, the mapping thread
+ * renders for visualisation).  Every step of that path runs in the library's own
+ * CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions for every call
+ *  - Return value: MAP_OK (0) on success, a negative MAP_E* code otherwise; the
+ *    message of the last failure is available from map_last_error().
+ *  - Camera model: pinhole K = {fx, fy, cx, cy}; pixel (u, v) casts its ray through
+ *    its centre (u + 1/2, v + 1/2); OpenCV axes (x right, y down, z forward);
+ *    c2w is the row-major 3x4 camera-to-world matrix [R | t].
+ *  - Images are row-major (v outer, u inner).
+ *  - mem_kind says where a caller buffer lives: MAP_MEM_HOST (ordinary or pinned
+ *    host memory) or MAP_MEM_DEVICE (device memory of the GPU that was current
+ *    when the map was created).  The caller owns every buffer it passes; the
+ *    library owns all state behind a map_handle.
+ *  - stream: a cudaStream_t (NULL = legacy default stream).  All work of a call
+ *    is ordered on that stream.  Calls that return a value to host memory
+ *    synchronise that stream before returning; the others return as soon as the
+ *    work is queued, and input buffers may be reused as soon as the call returns
+ *    (inputs are copied or staged before return).
+ *  - A map_handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef NERFMAP_H
+#define NERFMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MAP_OK 0
+#define MAP_EINVAL (-1)   /* bad argument: null pointer, size or configuration */
+#define MAP_ENOMEM (-2)   /* device memory or the map's HBM budget exhausted */
+#define MAP_ENOKF (-3)    /* map_step before any keyframe was added */
+#define MAP_ETIMEOUT (-4) /* a bounded device-side wait expired */
+#define MAP_ECUDA (-5)    /* a CUDA runtime call failed */
+
+#define MAP_MAX_LEVELS 32
+
+#define MAP_MEM_HOST 0
+#define MAP_MEM_DEVICE 1
+
+/* MLP arithmetic.  Hash features, compositing, loss, gradients and Adam are FP32
+ * in every mode; the MLP layers run on FP32 CUDA cores (plain form) or on the
+ * tensor cores with FP16 / BF16 operands and FP32 accumulation. */
+#define MAP_PREC_FP32 0
+#define MAP_PREC_FP16 1
+#define MAP_PREC_BF16 2
+
+/* map_step flags */
+#define MAP_STEP_NO_UPDATE 1u  /* compute loss and gradients, skip Adam, keep gradients */
+
+/*
+ * Field and step configuration (copied by map_create).
+ *
+ * Grid (Instant-NGP multiresolution hash encoding, the map of the paper's
+ * Sec. 3.4): n_levels tables of 2^log2_table entries, n_features = 2 floats per
+ * entry, level l at resolution level_res[l] (vertex coordinates 0..N_l).  A level
+ * whose (N_l + 1)^3 vertices fit in its table is indexed densely, otherwise by the
+ * spatial hash (x * 1 ^ y * 2654435761 ^ z * 805459861) mod 2^log2_table.
+ * MLP widths are fixed: enc_width 32 (L * F zero padded), density_hidden 64,
+ * geo_width 16, color_hidden 64.
+ *
+ * Sampling (Sec. 3.2, sampling 3D positions along the pixel's ray): step i of a
+ * ray is at t_i = near_t + i * step_t, i < n_steps, grid position
+ * x = (o + t d - grid_origin) * grid_inv_size; it is kept when 0 <= x_a < box_max[a]
+ * on every axis and, if occ_res > 0, its occupancy cell is set; the first
+ * max_samples kept steps are the ray's samples, each with delta_i = step_t.
+ *
+ * Occupancy (occ_res > 0): cell density EMA d <- max(occ_decay * d,
+ * sigma(x_cell)), bit = d > occ_thresh, refreshed every occ_every steps
+ * (0 = only by map_refresh_occupancy).
+ *
+ * Loss (Eq. mapping_loss): per ray ||I - I*||^2 + lambda_d (D - D*)^2 / Sigma_D,
+ * averaged over the rays of a step.  Adam: lr, beta1, beta2, eps, bias corrected.
+ * render_t_min: a render stops a ray once its transmittance falls below it.
+ */
+typedef struct map_config {
+    uint32_t n_levels;
+    uint32_t n_features;
+    uint32_t log2_table;
+    uint32_t level_res[MAP_MAX_LEVELS];
+    uint32_t enc_width;
+    uint32_t density_hidden;
+    uint32_t geo_width;
+    uint32_t color_hidden;
+    float near_t;
+    float step_t;
+    uint32_t n_steps;
+    uint32_t max_samples;
+    float grid_origin[3];
+    float grid_inv_size;
+    float box_max[3];
+    uint32_t occ_res;
+    uint32_t occ_every;
+    float occ_decay;
+    float occ_thresh;
+    float lambda_d;
+    float lr;
+    float beta1;
+    float beta2;
+    float eps;
+    float render_t_min;
+    uint32_t precision;
+    uint32_t reserved0;
+    uint64_t seed;
+} map_config;
+
+typedef struct map_scene* map_handle;
+
+/* Per-step counters of the last map_step / map_render (read back on request). */
+typedef struct map_stats {
+    uint64_t step;          /* completed optimisation steps (Adam t) */
+    uint64_t n_samples;     /* retained samples of the last step or render */
+    uint32_t n_rays;        /* rays of the last step or render */
+    uint32_t n_keyframes;   /* keyframes in the store */
+    uint64_t param_count;   /* FP32 parameters (tables then MLP weights) */
+    uint64_t device_bytes;  /* device memory held by the map */
+    uint64_t kernel_launches; /* kernels this map has launched since creation */
+} map_stats;
+
+/* Phases of a step or render, for map_profile_read. */
+#define MAP_PH_RAYGEN 0     /* ray draw and casting (a1) */
+#define MAP_PH_MARCH 1      /* march, occupancy test, count scan, emit (a2) */
+#define MAP_PH_FIELD_FWD 2  /* encoding, SH and both MLPs forward (a3-a6) */
+#define MAP_PH_COMPOSITE 3  /* compositing, loss and its per-sample gradient (a7-a9) */
+#define MAP_PH_FIELD_BWD 4  /* MLP backward and hash-table scatter (a10-a11) */
+#define MAP_PH_ADAM 5       /* Adam (a12) */
+#define MAP_PH_OCC 6        /* occupancy refresh (a13) */
+#define MAP_PH_OUTPUT 7     /* render output write */
+#define MAP_PHASES 8
+
+/*
+ * map_create - allocate a map on the current device.
+ * cfg: configuration (validated: 1 <= n_levels <= 16 (n_levels * n_features <= 32),
+ *   n_features == 2, 10 <= log2_table <= 24, level_res[l] >= 2, widths as above,
+ *   occ_res a multiple of 8 (or 0) and <= 1024, precision a MAP_PREC_* value).
+ * hbm_budget_bytes: upper bound on the device memory this map may hold, counting
+ *   parameters, gradients, Adam moments, occupancy, keyframes and step workspace
+ *   (0 = no bound).  Any allocation beyond it fails with MAP_ENOMEM.
+ * out: receives the handle.  Parameters start seeded from cfg->seed: tables
+ *   U(-1e-4, 1e-4), MLP weights N(0, 0.05).
+ */
+int map_create(const map_config* cfg, size_t hbm_budget_bytes, map_handle* out);
+
+/* map_destroy - synchronise the device and free everything the map holds. */
+int map_destroy(map_handle h);
+
+/*
+ * map_add_keyframe - hand a keyframe to the mapper (Sec. 3.3: the tracking
+ * thread sends poses, images, depth maps and depth covariances of its window).
+ * A kf_id already in the store is replaced in place (the window is re-sent with
+ * refined poses and depths); a new id is appended.
+ * c2w[12], K[4]: host memory.  rgb: H*W*3 floats in [0,1]; depth: H*W floats;
+ * depth_var: H*W per-pixel variances Sigma_D (> 0).  depth_is_z != 0: depth and
+ * variance are z-depth values and are converted to distance along the unit ray
+ * (D * s and Sigma_D * s^2 with s = ||K^-1 [u+1/2, v+1/2, 1]||); 0: already ray
+ * distances.  rgb, depth, depth_var live in mem_kind memory.
+ */
+int map_add_keyframe(map_handle h, uint32_t kf_id, const float c2w[12], const float K[4],
+                     uint32_t W, uint32_t H, const float* rgb, const float* depth,
+                     const float* depth_var, int depth_is_z, int mem_kind, void* stream);
+
+/*
+ * map_step - one mapping step (Sec. 3.2-3.3): draw n_rays rays uniformly over all
+ * keyframes (with replacement, SplitMix64 counter generator keyed by seed and the
+ * step counter), march, encode, evaluate the MLPs, composite colour and expected
+ * depth, evaluate L_M, back-propagate to the tables and MLP weights and apply
+ * Adam (unless MAP_STEP_NO_UPDATE).  The ray draw of the k-th call uses step
+ * index k = map_stats.step before the call (NO_UPDATE calls do not advance it).
+ * out_loss: host pointer or NULL; when set, the call waits for the step and stores
+ * L_M there.  n_rays: 1 .. 2^24.
+ */
+int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float* out_loss,
+             void* stream);
+
+/* map_loss_device - device address of the FP32 loss of the last step (valid until
+ * the next step on the handle); lets a caller read it without a host wait. */
+const float* map_loss_device(map_handle h);
+
+/*
+ * map_render - forward-only render of a W x H view (Sec. 3.3).  out_rgb: H*W*3
+ * floats, out_depth: H*W floats (expected ray-termination distance along the unit
+ * ray), both in mem_kind memory; either may be NULL.  out_acc (nullable, same
+ * memory kind): H*W accumulated opacities.  Rays stop once transmittance drops
+ * below cfg.render_t_min.
+ */
+int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, uint32_t H,
+               float* out_rgb, float* out_depth, float* out_acc, int mem_kind, void* stream);
+
+/* Parameter I/O.  Layout (FP32): tables [L][2^log2_table][F], then W1 [64][32],
+ * W2 [16][64], W3 [64][32], W4 [64][64], W5 [3][64], each (out, in) row-major.
+ * n must equal map_stats.param_count.  get/set wait for the stream. */
+int map_get_params(map_handle h, float* dst, size_t n, int mem_kind, void* stream);
+int map_set_params(map_handle h, const float* src, size_t n, int mem_kind, void* stream);
+/* Gradient of L_M from the last step (meaningful after MAP_STEP_NO_UPDATE). */
+int map_get_grads(map_handle h, float* dst, size_t n, int mem_kind, void* stream);
+/* Adam moments m, v (either may be NULL) and a reset of the optimiser state. */
+int map_get_adam(map_handle h, float* m, float* v, size_t n, int mem_kind, void* stream);
+int map_reset_adam(map_handle h, void* stream);
+
+/*
+ * Occupancy.  bits: occ_res^3 / 8 bytes, cell (cx, cy, cz) at linear index
+ * b = cx + occ_res * (cy + occ_res * cz) is bit (b & 7) of byte (b >> 3).
+ * density: occ_res^3 floats (the EMA).  map_set_occupancy also sets the EMA of
+ * set cells to 1 and of clear cells to 0.  map_refresh_occupancy runs one refresh
+ * now (refresh index = number of refreshes so far).
+ */
+int map_set_occupancy(map_handle h, const uint8_t* bits, size_t n_bytes, int mem_kind,
+                      void* stream);
+int map_get_occupancy(map_handle h, uint8_t* bits, float* density, int mem_kind, void* stream);
+int map_set_occupancy_density(map_handle h, const float* density, size_t n, int mem_kind,
+                              void* stream);
+int map_refresh_occupancy(map_handle h, void* stream);
+
+/* Inspection of the last step or render (for tests and tools); waits for the
+ * stream.  Copies min(cap, n_samples) samples: ray index and t of each retained
+ * sample in ray-major order, and per ray the rendered colour (3), depth and
+ * opacity.  Any pointer may be NULL. */
+int map_get_samples(map_handle h, uint32_t* ray_id, float* t, size_t cap, void* stream);
+int map_get_ray_outputs(map_handle h, float* rgb, float* depth, float* acc, size_t n_rays,
+                        void* stream);
+
+int map_get_stats(map_handle h, map_stats* out);
+
+/* Phase timing with CUDA events recorded on the caller's stream around each phase
+ * of every subsequent step / render.  map_profile_enable(h, 1) starts (and clears)
+ * the record, (h, 0) stops it.  map_profile_read waits for the recorded events and
+ * returns, per MAP_PH_* phase, the summed milliseconds and the number of phase
+ * executions and kernel launches (arrays of MAP_PHASES entries, any may be NULL). */
+int map_profile_enable(map_handle h, int enable);
+int map_profile_read(map_handle h, double* ms, uint64_t* count, uint64_t* launches);
+
+/* sizeof(map_config) as compiled into the library, so a binding can check that its
+ * own copy of the struct has the same layout. */
+size_t map_abi_config_size(void);
+
+/* Message of the last failure on h (h = NULL: of the last failed map_create). */
+const char* map_last_error(map_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NERFMAP_H */

@@ -1,0 +1,365 @@
+"""ctypes binding of libnerfmap.so (include/nerfmap.h), argument marshalling only.
+
+Every computation of the mapping path runs in the library's CUDA kernels; this
+module converts configurations, numpy arrays and torch tensors to the C ABI's plain
+pointers and sizes.  It fails loudly when the library is missing: there is no CPU
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnerfmap.so")
+
+MAP_OK, MAP_EINVAL, MAP_ENOMEM, MAP_ENOKF, MAP_ETIMEOUT, MAP_ECUDA = 0, -1, -2, -3, -4, -5
+MAP_MEM_HOST, MAP_MEM_DEVICE = 0, 1
+MAP_STEP_NO_UPDATE = 1
+PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2}
+MLP_SHAPES = [("W1", (64, 32)), ("W2", (16, 64)), ("W3", (64, 32)), ("W4", (64, 64)), ("W5", (3, 64))]
+MLP_PARAMS = sum(a * b for _, (a, b) in MLP_SHAPES)
+
+
+class MapError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"nerfmap error {code}: {msg}")
+        self.code = code
+
+
+class MapConfig(ctypes.Structure):
+    _fields_ = [
+        ("n_levels", ctypes.c_uint32), ("n_features", ctypes.c_uint32),
+        ("log2_table", ctypes.c_uint32), ("level_res", ctypes.c_uint32 * 32),
+        ("enc_width", ctypes.c_uint32), ("density_hidden", ctypes.c_uint32),
+        ("geo_width", ctypes.c_uint32), ("color_hidden", ctypes.c_uint32),
+        ("near_t", ctypes.c_float), ("step_t", ctypes.c_float),
+        ("n_steps", ctypes.c_uint32), ("max_samples", ctypes.c_uint32),
+        ("grid_origin", ctypes.c_float * 3), ("grid_inv_size", ctypes.c_float),
+        ("box_max", ctypes.c_float * 3), ("occ_res", ctypes.c_uint32),
+        ("occ_every", ctypes.c_uint32), ("occ_decay", ctypes.c_float),
+        ("occ_thresh", ctypes.c_float), ("lambda_d", ctypes.c_float), ("lr", ctypes.c_float),
+        ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+        ("render_t_min", ctypes.c_float), ("precision", ctypes.c_uint32),
+        ("reserved0", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+    ]
+
+
+class MapStats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_uint64), ("n_samples", ctypes.c_uint64), ("n_rays", ctypes.c_uint32),
+                ("n_keyframes", ctypes.c_uint32), ("param_count", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+
+
+PHASES = ["ray_gen", "march", "field_fwd", "composite", "field_bwd", "adam", "occupancy", "output"]
+
+
+_SIGS = {
+    "map_create": (ctypes.c_int, [ctypes.POINTER(MapConfig), ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+    "map_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "map_add_keyframe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "map_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                ctypes.c_void_p, ctypes.c_void_p]),
+    "map_loss_device": (ctypes.c_void_p, [ctypes.c_void_p]),
+    "map_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                  ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_int, ctypes.c_void_p]),
+    "map_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
+    "map_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
+    "map_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
+    "map_get_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                    ctypes.c_int, ctypes.c_void_p]),
+    "map_reset_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "map_set_occupancy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
+    "map_get_occupancy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "map_set_occupancy_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                                 ctypes.c_void_p]),
+    "map_refresh_occupancy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "map_get_samples": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "map_get_ray_outputs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_size_t, ctypes.c_void_p]),
+    "map_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MapStats)]),
+    "map_abi_config_size": (ctypes.c_size_t, []),
+    "map_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "map_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "map_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def exported_symbols() -> list:
+    return list(_SIGS)
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libnerfmap.so (built in-tree by build.build()); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnerfmap.so not built at {path}: run paper_2210_13641_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if lib.map_abi_config_size() != ctypes.sizeof(MapConfig):
+        raise RuntimeError("map_config layout mismatch between the binding and libnerfmap.so")
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------ config helpers
+
+def level_resolutions(n_levels: int, n_min: int, growth: Optional[float] = None,
+                      n_max: Optional[int] = None) -> list:
+    """N_l = floor(N_min * b^l) with b = growth or (N_max/N_min)^(1/(L-1)); a 1e-9
+    relative nudge keeps exact integers (e.g. 16 * 128 = 2048) from flooring below."""
+    if growth is None:
+        growth = (n_max / n_min) ** (1.0 / (n_levels - 1)) if n_levels > 1 else 1.0
+    return [int(math.floor(n_min * growth ** l * (1.0 + 1e-9))) for l in range(n_levels)]
+
+
+def make_config(cfg, occ_every: Optional[int] = None) -> MapConfig:
+    """C configuration from a field-config object (attributes as in the header)."""
+    c = MapConfig()
+    c.n_levels = cfg.n_levels
+    c.n_features = cfg.n_features
+    c.log2_table = cfg.log2_table
+    res = level_resolutions(cfg.n_levels, cfg.n_min, cfg.growth, cfg.n_max)
+    for l, n in enumerate(res):
+        c.level_res[l] = n
+    c.enc_width, c.density_hidden, c.geo_width, c.color_hidden = 32, 64, 16, 64
+    c.near_t = float(cfg.near)
+    c.step_t = float(cfg.step)
+    c.n_steps = cfg.n_steps
+    c.max_samples = cfg.max_samples
+    for a in range(3):
+        c.grid_origin[a] = float(cfg.grid_origin[a])
+        c.box_max[a] = float(cfg.box_max[a])
+    c.grid_inv_size = float(cfg.grid_inv_size)
+    c.occ_res = cfg.occ_res
+    c.occ_every = cfg.occ_every if occ_every is None else occ_every
+    c.occ_decay = float(cfg.occ_decay)
+    c.occ_thresh = float(cfg.occ_thresh)
+    c.lambda_d = float(cfg.lambda_d)
+    c.lr, c.beta1, c.beta2, c.eps = float(cfg.lr), float(cfg.beta1), float(cfg.beta2), float(cfg.eps)
+    c.render_t_min = float(cfg.render_t_min)
+    c.precision = PRECISION[cfg.precision]
+    c.seed = cfg.seed
+    return c
+
+
+def pack_params(named: dict) -> np.ndarray:
+    """Named parameters -> flat FP32 vector in the library layout."""
+    parts = [np.ascontiguousarray(named["tables"], np.float32).ravel()]
+    parts += [np.ascontiguousarray(named[k], np.float32).ravel() for k, _ in MLP_SHAPES]
+    return np.concatenate(parts)
+
+
+def unpack_params(flat: np.ndarray, n_levels: int, log2_table: int, n_features: int = 2) -> dict:
+    T = 1 << log2_table
+    nt = n_levels * T * n_features
+    out = {"tables": flat[:nt].reshape(n_levels, T, n_features)}
+    off = nt
+    for k, (a, b) in MLP_SHAPES:
+        out[k] = flat[off:off + a * b].reshape(a, b)
+        off += a * b
+    return out
+
+
+# ------------------------------------------------------------------ pointers
+
+def _ptr(x):
+    """(address, mem_kind) of a numpy array or torch tensor (None -> (None, host))."""
+    if x is None:
+        return None, MAP_MEM_HOST
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data, MAP_MEM_HOST
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr(), (MAP_MEM_DEVICE if x.is_cuda else MAP_MEM_HOST)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class NerfMap:
+    """One map (hash tables, MLP weights, Adam state, occupancy, keyframes) on the
+    current GPU, driven through the C ABI."""
+
+    def __init__(self, cfg, hbm_budget: int = 0, occ_every: Optional[int] = None):
+        self.lib = load()
+        self.cfg = cfg
+        self.ccfg = make_config(cfg, occ_every)
+        h = ctypes.c_void_p()
+        rc = self.lib.map_create(ctypes.byref(self.ccfg), hbm_budget, ctypes.byref(h))
+        if rc != MAP_OK:
+            raise MapError(rc, self.lib.map_last_error(None).decode())
+        self.h = h
+        self.n_params = self.stats().param_count
+
+    def _check(self, rc):
+        if rc != MAP_OK:
+            raise MapError(rc, self.lib.map_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.map_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- keyframes
+    def add_keyframe(self, kf, rgb=None, depth=None, var=None, stream=None):
+        """kf: object with kf_id, c2w [3,4], K [4], W, H, rgb, depth, var, depth_is_z.
+        rgb/depth/var override the arrays (e.g. torch tensors on the device)."""
+        c2w = np.ascontiguousarray(kf.c2w, np.float32).reshape(12)
+        K = np.ascontiguousarray(kf.K, np.float32).reshape(4)
+        rgb = np.ascontiguousarray(kf.rgb, np.float32) if rgb is None else rgb
+        depth = np.ascontiguousarray(kf.depth, np.float32) if depth is None else depth
+        var = np.ascontiguousarray(kf.var, np.float32) if var is None else var
+        (pr, kind), (pd, _), (pv, _) = _ptr(rgb), _ptr(depth), _ptr(var)
+        self._check(self.lib.map_add_keyframe(self.h, kf.kf_id, c2w.ctypes.data, K.ctypes.data, kf.W, kf.H,
+                                              pr, pd, pv, int(bool(kf.depth_is_z)), kind, _stream(stream)))
+
+    # -------------------------------------------------------------- step / render
+    def step(self, n_rays: int, seed: int, no_update: bool = False, want_loss: bool = True, stream=None):
+        loss = ctypes.c_float()
+        flags = MAP_STEP_NO_UPDATE if no_update else 0
+        self._check(self.lib.map_step(self.h, n_rays, seed, flags,
+                                      ctypes.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None
+
+    def loss_device_ptr(self) -> int:
+        return self.lib.map_loss_device(self.h)
+
+    def render(self, c2w, K, W: int, H: int, out_rgb=None, out_depth=None, out_acc=None, stream=None):
+        """Renders into the given buffers (torch CUDA tensors or numpy arrays); with no
+        buffers, returns host numpy arrays (rgb [H,W,3], depth [H,W], acc [H,W])."""
+        c2w = np.ascontiguousarray(c2w, np.float32).reshape(12)
+        K = np.ascontiguousarray(K, np.float32).reshape(4)
+        if out_rgb is None and out_depth is None and out_acc is None:
+            out_rgb = np.zeros((H, W, 3), np.float32)
+            out_depth = np.zeros((H, W), np.float32)
+            out_acc = np.zeros((H, W), np.float32)
+        (p1, kind), (p2, k2), (p3, k3) = _ptr(out_rgb), _ptr(out_depth), _ptr(out_acc)
+        if out_rgb is None:
+            kind = k2 if out_depth is not None else k3
+        self._check(self.lib.map_render(self.h, c2w.ctypes.data, K.ctypes.data, W, H, p1, p2, p3, kind,
+                                        _stream(stream)))
+        return out_rgb, out_depth, out_acc
+
+    # -------------------------------------------------------------- parameters
+    def get_params(self, out=None, stream=None) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32) if out is None else out
+        p, kind = _ptr(out)
+        self._check(self.lib.map_get_params(self.h, p, self.n_params, kind, _stream(stream)))
+        return out
+
+    def set_params(self, flat, stream=None):
+        if isinstance(flat, dict):
+            flat = pack_params(flat)
+        if isinstance(flat, np.ndarray):
+            flat = np.ascontiguousarray(flat, np.float32)
+        p, kind = _ptr(flat)
+        self._check(self.lib.map_set_params(self.h, p, self.n_params, kind, _stream(stream)))
+
+    def get_grads(self, out=None, stream=None) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32) if out is None else out
+        p, kind = _ptr(out)
+        self._check(self.lib.map_get_grads(self.h, p, self.n_params, kind, _stream(stream)))
+        return out
+
+    def get_adam(self, stream=None):
+        m = np.zeros(self.n_params, np.float32)
+        v = np.zeros(self.n_params, np.float32)
+        self._check(self.lib.map_get_adam(self.h, m.ctypes.data, v.ctypes.data, self.n_params, MAP_MEM_HOST,
+                                          _stream(stream)))
+        return m, v
+
+    def reset_adam(self, stream=None):
+        self._check(self.lib.map_reset_adam(self.h, _stream(stream)))
+
+    def unpack(self, flat) -> dict:
+        return unpack_params(flat, self.cfg.n_levels, self.cfg.log2_table, self.cfg.n_features)
+
+    # -------------------------------------------------------------- occupancy
+    def set_occupancy(self, bits: np.ndarray, stream=None):
+        bits = np.ascontiguousarray(bits, np.uint8)
+        self._check(self.lib.map_set_occupancy(self.h, bits.ctypes.data, bits.size, MAP_MEM_HOST, _stream(stream)))
+
+    def set_occupancy_density(self, dens: np.ndarray, stream=None):
+        dens = np.ascontiguousarray(dens, np.float32)
+        self._check(self.lib.map_set_occupancy_density(self.h, dens.ctypes.data, dens.size, MAP_MEM_HOST,
+                                                       _stream(stream)))
+
+    def get_occupancy(self, stream=None):
+        n = self.cfg.occ_res ** 3
+        bits = np.zeros(n // 8, np.uint8)
+        dens = np.zeros(n, np.float32)
+        self._check(self.lib.map_get_occupancy(self.h, bits.ctypes.data, dens.ctypes.data, MAP_MEM_HOST,
+                                               _stream(stream)))
+        return bits, dens
+
+    def refresh_occupancy(self, stream=None):
+        self._check(self.lib.map_refresh_occupancy(self.h, _stream(stream)))
+
+    # -------------------------------------------------------------- inspection
+    def stats(self) -> MapStats:
+        s = MapStats()
+        self._check(self.lib.map_get_stats(self.h, ctypes.byref(s)))
+        return s
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.map_profile_enable(self.h, int(enable)))
+
+    def profile_read(self) -> dict:
+        ms = np.zeros(8, np.float64)
+        cnt = np.zeros(8, np.uint64)
+        lch = np.zeros(8, np.uint64)
+        self._check(self.lib.map_profile_read(self.h, ms.ctypes.data, cnt.ctypes.data, lch.ctypes.data))
+        return {name: dict(ms=float(ms[i]), count=int(cnt[i]), launches=int(lch[i]))
+                for i, name in enumerate(PHASES)}
+
+    def samples(self):
+        n = self.stats().n_samples
+        rid = np.zeros(n, np.uint32)
+        t = np.zeros(n, np.float32)
+        self._check(self.lib.map_get_samples(self.h, rid.ctypes.data, t.ctypes.data, n, None))
+        return rid, t
+
+    def ray_outputs(self, n_rays: int):
+        rgb = np.zeros((n_rays, 3), np.float32)
+        d = np.zeros(n_rays, np.float32)
+        a = np.zeros(n_rays, np.float32)
+        self._check(self.lib.map_get_ray_outputs(self.h, rgb.ctypes.data, d.ctypes.data, a.ctypes.data, n_rays,
+                                                 None))
+        return rgb, d, a

@@ -1,0 +1,653 @@
+// api.cu - the C ABI declared in include/nerfmap.h: map state in device memory,
+// keyframe store, and the stream-ordered launch sequence of one mapping step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nerfmap.h"
+#include "internal.h"
+
+using namespace nm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Keyframe {
+    uint32_t id, W, H;
+    float4* texels;
+    size_t bytes;
+};
+
+struct PhaseRec {
+    int phase;
+    cudaEvent_t a, b;
+    uint32_t launches;
+};
+
+}  // namespace
+
+struct map_scene {
+    map_config cfg;
+    DevCfg dc;
+    int device = 0;
+    int n_sm = 0;
+    size_t budget = 0, held = 0;
+    std::vector<std::pair<void*, size_t>> allocs;
+
+    float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+    size_t n_params = 0, n_table = 0;
+    uint32_t* occ_bits = nullptr;
+    float* occ_density = nullptr;
+    uint32_t n_cells = 0;
+
+    std::vector<Keyframe> kfs;
+    std::vector<KfDesc> kf_desc;
+    KfDesc* d_kfs = nullptr;
+    uint32_t d_kfs_cap = 0;
+    float* staging = nullptr;       // keyframe upload staging (rgb, depth, var)
+    size_t staging_floats = 0;
+
+    StepBufs bufs{};
+    std::vector<void*> buf_allocs;
+
+    uint64_t step = 0, n_refresh = 0;
+    bool grads_dirty = false;
+    uint32_t last_rays = 0;
+    cudaStream_t last_stream = nullptr;
+    uint64_t launches = 0;
+    bool prof_on = false;
+    std::vector<PhaseRec> prof;
+    std::string err;
+};
+
+namespace {
+
+int fail(map_scene* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(map_scene* h, cudaError_t e, const char* what) {
+    return fail(h, MAP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define NM_CUDA(h, call)                                      \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+int dalloc(map_scene* h, void** p, size_t bytes) {
+    if (h->budget && h->held + bytes > h->budget)
+        return fail(h, MAP_ENOMEM, "HBM budget exceeded (" + std::to_string(h->held + bytes) + " > " +
+                                       std::to_string(h->budget) + " bytes)");
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, MAP_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->held += bytes;
+    h->allocs.emplace_back(*p, bytes);
+    return MAP_OK;
+}
+
+void dfree(map_scene* h, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < h->allocs.size(); ++i) {
+        if (h->allocs[i].first == p) {
+            h->held -= h->allocs[i].second;
+            h->allocs.erase(h->allocs.begin() + i);
+            break;
+        }
+    }
+    cudaFree(p);
+}
+
+int validate(const map_config* c, std::string& why) {
+    if (!c) return why = "null config", MAP_EINVAL;
+    if (c->n_levels < 1 || c->n_levels > 16) return why = "n_levels must be 1..16", MAP_EINVAL;
+    if (c->n_features != 2) return why = "n_features must be 2", MAP_EINVAL;
+    if (c->log2_table < 10 || c->log2_table > 24) return why = "log2_table must be 10..24", MAP_EINVAL;
+    for (uint32_t l = 0; l < c->n_levels; ++l)
+        if (c->level_res[l] < 2 || c->level_res[l] > (1u << 20)) return why = "level_res out of range", MAP_EINVAL;
+    if (c->enc_width != 32 || c->density_hidden != 64 || c->geo_width != 16 || c->color_hidden != 64)
+        return why = "MLP widths must be 32/64/16/64", MAP_EINVAL;
+    if (!(c->step_t > 0.f) || c->n_steps == 0 || c->n_steps > 65536) return why = "bad march", MAP_EINVAL;
+    if (c->max_samples == 0 || c->max_samples > 1024) return why = "max_samples must be 1..1024", MAP_EINVAL;
+    if (c->occ_res % 8 != 0 || c->occ_res > 1024) return why = "occ_res must be a multiple of 8, <= 1024", MAP_EINVAL;
+    if (!(c->grid_inv_size > 0.f)) return why = "grid_inv_size must be > 0", MAP_EINVAL;
+    if (c->precision > 2) return why = "precision must be 0, 1 or 2", MAP_EINVAL;
+    return MAP_OK;
+}
+
+int ensure_step_bufs(map_scene* h, uint32_t n_rays) {
+    const uint64_t need_samples = (uint64_t)n_rays * h->cfg.max_samples;
+    const bool need_feat = true;
+    if (h->bufs.cap_rays >= n_rays && h->bufs.cap_samples >= need_samples) return MAP_OK;
+    cudaDeviceSynchronize();
+    for (void* p : h->buf_allocs) dfree(h, p);
+    h->buf_allocs.clear();
+    StepBufs b{};
+    const uint32_t cap = std::max<uint32_t>(n_rays, 1024);
+    const uint64_t cs = (uint64_t)cap * h->cfg.max_samples;
+    const uint32_t n_tiles = (cap + 4095) / 4096;
+    struct Req { void** p; size_t bytes; };
+    std::vector<Req> reqs = {
+        {(void**)&b.rays, sizeof(float) * kRayPlanes * cap},
+        {(void**)&b.counts, sizeof(uint32_t) * cap},
+        {(void**)&b.offsets, sizeof(uint32_t) * (cap + 1)},
+        {(void**)&b.block_sums, sizeof(uint32_t) * (n_tiles + 1)},
+        {(void**)&b.ray_id, sizeof(uint32_t) * cs},
+        {(void**)&b.t, sizeof(float) * cs},
+        {(void**)&b.sig_rgb, sizeof(float4) * cs},
+        {(void**)&b.dsig_rgb, sizeof(float4) * cs},
+        {(void**)&b.ray_out, sizeof(float) * 5 * cap},
+        {(void**)&b.loss, 64},
+        {(void**)&b.err, 64},
+    };
+    if (need_feat) reqs.push_back({(void**)&b.feat, sizeof(float) * kEnc * cs});
+    for (auto& r : reqs) {
+        int rc = dalloc(h, r.p, r.bytes);
+        if (rc) {
+            for (void* p : h->buf_allocs) dfree(h, p);
+            h->buf_allocs.clear();
+            h->bufs = StepBufs{};
+            return rc;
+        }
+        h->buf_allocs.push_back(*r.p);
+    }
+    b.cap_rays = cap;
+    b.cap_samples = cs;
+    cudaMemset(b.loss, 0, 64);
+    cudaMemset(b.err, 0, 64);
+    h->bufs = b;
+    return MAP_OK;
+}
+
+void fill_devcfg(map_scene* h) {
+    const map_config& c = h->cfg;
+    DevCfg& d = h->dc;
+    std::memset(&d, 0, sizeof(d));
+    d.L = c.n_levels;
+    d.log2T = c.log2_table;
+    d.T = 1u << c.log2_table;
+    d.dense_mask = 0;
+    for (uint32_t l = 0; l < c.n_levels; ++l) {
+        d.res[l] = c.level_res[l];
+        const uint64_t s = (uint64_t)c.level_res[l] + 1;
+        if (s * s * s <= d.T) d.dense_mask |= 1u << l;
+    }
+    d.near_t = c.near_t;
+    d.step_t = c.step_t;
+    d.n_steps = c.n_steps;
+    d.max_samples = c.max_samples;
+    for (int a = 0; a < 3; ++a) {
+        d.org[a] = c.grid_origin[a];
+        d.box[a] = c.box_max[a];
+    }
+    d.inv_size = c.grid_inv_size;
+    d.occ_res = c.occ_res;
+    d.lambda_d = c.lambda_d;
+    d.t_min = 0.f;
+}
+
+int copy_in(map_scene* h, void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_t s) {
+    const cudaMemcpyKind k = mem_kind == MAP_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    NM_CUDA(h, cudaMemcpyAsync(dst, src, bytes, k, s));
+    return MAP_OK;
+}
+
+int copy_out(map_scene* h, void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_t s) {
+    const cudaMemcpyKind k = mem_kind == MAP_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    NM_CUDA(h, cudaMemcpyAsync(dst, src, bytes, k, s));
+    NM_CUDA(h, cudaStreamSynchronize(s));
+    return MAP_OK;
+}
+
+int check_launch(map_scene* h, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    return MAP_OK;
+}
+
+const char* const kPhaseName[MAP_PHASES] = {"ray_gen", "march", "field_fwd", "composite",
+                                             "field_bwd", "adam", "occupancy", "output"};
+
+// Runs one phase: optional CUDA events around it on the stream, launch check and
+// launch accounting.
+template <class F>
+int phase(map_scene* h, int ph, uint32_t n_launch, cudaStream_t s, F&& f) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (h->prof_on) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    f();
+    int rc = check_launch(h, kPhaseName[ph]);
+    if (h->prof_on) {
+        cudaEventRecord(b, s);
+        h->prof.push_back(PhaseRec{ph, a, b, n_launch});
+    }
+    h->launches += n_launch;
+    return rc;
+}
+
+void prof_clear(map_scene* h) {
+    for (auto& r : h->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    h->prof.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int map_create(const map_config* cfg, size_t hbm_budget_bytes, map_handle* out) {
+    std::string why;
+    if (!out) return fail(nullptr, MAP_EINVAL, "null output handle");
+    *out = nullptr;
+    if (validate(cfg, why) != MAP_OK) return fail(nullptr, MAP_EINVAL, why);
+    map_scene* h = new map_scene();
+    h->cfg = *cfg;
+    h->budget = hbm_budget_bytes;
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    fill_devcfg(h);
+    h->n_table = (size_t)cfg->n_levels * (1u << cfg->log2_table) * 2;
+    h->n_params = h->n_table + kMlpParams;
+    const size_t pb = h->n_params * sizeof(float);
+    int rc = MAP_OK;
+    if (!rc) rc = dalloc(h, (void**)&h->params, pb);
+    if (!rc) rc = dalloc(h, (void**)&h->grads, pb);
+    if (!rc) rc = dalloc(h, (void**)&h->adam_m, pb);
+    if (!rc) rc = dalloc(h, (void**)&h->adam_v, pb);
+    if (!rc && cfg->occ_res) {
+        h->n_cells = cfg->occ_res * cfg->occ_res * cfg->occ_res;
+        rc = dalloc(h, (void**)&h->occ_bits, h->n_cells / 8);
+        if (!rc) rc = dalloc(h, (void**)&h->occ_density, h->n_cells * sizeof(float));
+    }
+    if (rc) {
+        g_create_error = h->err;
+        map_destroy(h);
+        return rc;
+    }
+    cudaMemset(h->grads, 0, pb);
+    cudaMemset(h->adam_m, 0, pb);
+    cudaMemset(h->adam_v, 0, pb);
+    if (h->occ_bits) {
+        cudaMemset(h->occ_bits, 0xFF, h->n_cells / 8);  // all occupied until set or refreshed
+        launch_occ_from_bits(h->occ_bits, h->occ_density, h->n_cells, nullptr);
+    }
+    launch_init_params(h->params, h->n_table, cfg->seed, nullptr);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        g_create_error = std::string("init: ") + cudaGetErrorString(e);
+        map_destroy(h);
+        return MAP_ECUDA;
+    }
+    *out = h;
+    return MAP_OK;
+}
+
+int map_destroy(map_handle h) {
+    if (!h) return MAP_EINVAL;
+    cudaDeviceSynchronize();
+    prof_clear(h);
+    for (auto& a : h->allocs) cudaFree(a.first);
+    h->allocs.clear();
+    delete h;
+    return MAP_OK;
+}
+
+int map_add_keyframe(map_handle h, uint32_t kf_id, const float c2w[12], const float K[4], uint32_t W,
+                     uint32_t H, const float* rgb, const float* depth, const float* depth_var,
+                     int depth_is_z, int mem_kind, void* stream) {
+    if (!h) return MAP_EINVAL;
+    if (!c2w || !K || !rgb || !depth || !depth_var) return fail(h, MAP_EINVAL, "null keyframe input");
+    if (W == 0 || H == 0 || (uint64_t)W * H > (1ull << 26)) return fail(h, MAP_EINVAL, "bad keyframe size");
+    if (!(K[0] > 0.f) || !(K[1] > 0.f)) return fail(h, MAP_EINVAL, "focal lengths must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    const size_t npx = (size_t)W * H;
+    size_t idx = h->kfs.size();
+    for (size_t i = 0; i < h->kfs.size(); ++i)
+        if (h->kfs[i].id == kf_id) idx = i;
+    if (idx < h->kfs.size() && (h->kfs[idx].W != W || h->kfs[idx].H != H)) {
+        cudaStreamSynchronize(s);
+        dfree(h, h->kfs[idx].texels);
+        h->kfs[idx].texels = nullptr;
+    }
+    if (idx == h->kfs.size()) h->kfs.push_back(Keyframe{kf_id, W, H, nullptr, 0});
+    Keyframe& kf = h->kfs[idx];
+    kf.W = W;
+    kf.H = H;
+    if (!kf.texels) {
+        int rc = dalloc(h, (void**)&kf.texels, npx * 2 * sizeof(float4));
+        if (rc) {
+            // drop the entry (new, or replaced at a new size) and republish the table
+            h->kfs.erase(h->kfs.begin() + idx);
+            if (idx < h->kf_desc.size()) h->kf_desc.erase(h->kf_desc.begin() + idx);
+            if (h->d_kfs && !h->kf_desc.empty())
+                copy_in(h, h->d_kfs, h->kf_desc.data(), h->kf_desc.size() * sizeof(KfDesc), MAP_MEM_HOST, s);
+            return fail(h, rc, h->err);
+        }
+        kf.bytes = npx * 2 * sizeof(float4);
+    }
+    const float *d_rgb = rgb, *d_depth = depth, *d_var = depth_var;
+    if (mem_kind != MAP_MEM_DEVICE) {
+        if (h->staging_floats < npx * 5) {
+            cudaStreamSynchronize(s);
+            dfree(h, h->staging);
+            h->staging = nullptr;
+            int rc = dalloc(h, (void**)&h->staging, npx * 5 * sizeof(float));
+            if (rc) return rc;
+            h->staging_floats = npx * 5;
+        }
+        int rc = copy_in(h, h->staging, rgb, npx * 3 * sizeof(float), MAP_MEM_HOST, s);
+        if (!rc) rc = copy_in(h, h->staging + npx * 3, depth, npx * sizeof(float), MAP_MEM_HOST, s);
+        if (!rc) rc = copy_in(h, h->staging + npx * 4, depth_var, npx * sizeof(float), MAP_MEM_HOST, s);
+        if (rc) return rc;
+        d_rgb = h->staging;
+        d_depth = h->staging + npx * 3;
+        d_var = h->staging + npx * 4;
+    }
+    launch_keyframe_texels(d_rgb, d_depth, d_var, W, H, K, depth_is_z, kf.texels, s);
+    int rc = check_launch(h, "keyframe texels");
+    if (rc) return rc;
+    // device keyframe table
+    KfDesc dsc;
+    std::memcpy(dsc.c2w, c2w, sizeof(dsc.c2w));
+    std::memcpy(dsc.K, K, sizeof(dsc.K));
+    dsc.W = W;
+    dsc.H = H;
+    dsc.texels = kf.texels;
+    if (h->kf_desc.size() <= idx) h->kf_desc.resize(idx + 1);
+    h->kf_desc[idx] = dsc;
+    if (h->d_kfs_cap < h->kf_desc.size()) {
+        cudaStreamSynchronize(s);
+        dfree(h, h->d_kfs);
+        h->d_kfs = nullptr;
+        const uint32_t cap = std::max<uint32_t>(64, (uint32_t)h->kf_desc.size() * 2);
+        rc = dalloc(h, (void**)&h->d_kfs, cap * sizeof(KfDesc));
+        if (rc) return rc;
+        h->d_kfs_cap = cap;
+    }
+    // pageable source: staged before the call returns, so kf_desc may change afterwards
+    return copy_in(h, h->d_kfs, h->kf_desc.data(), h->kf_desc.size() * sizeof(KfDesc), MAP_MEM_HOST, s);
+}
+
+static int run_forward(map_scene* h, uint32_t n_rays, bool train, cudaStream_t s) {
+    const StepBufs& b = h->bufs;
+    int rc = phase(h, MAP_PH_MARCH, 5, s, [&] { launch_march(h->dc, h->occ_bits, n_rays, b, s); });
+    if (rc) return rc;
+    return phase(h, MAP_PH_FIELD_FWD, 1, s,
+                 [&] { launch_field_fwd_fp32(h->dc, h->params, n_rays, b, train, h->n_sm, s); });
+}
+
+int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float* out_loss, void* stream) {
+    if (!h) return MAP_EINVAL;
+    if (n_rays == 0 || n_rays > (1u << 24)) return fail(h, MAP_EINVAL, "n_rays must be 1..2^24");
+    if (h->kfs.empty()) return fail(h, MAP_ENOKF, "no keyframes");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    int rc = ensure_step_bufs(h, n_rays);
+    if (rc) return rc;
+    if (h->grads_dirty) {
+        NM_CUDA(h, cudaMemsetAsync(h->grads, 0, h->n_params * sizeof(float), s));
+        h->grads_dirty = false;
+    }
+    const StepBufs& b = h->bufs;
+    rc = phase(h, MAP_PH_RAYGEN, 1, s,
+               [&] { launch_ray_gen(h->d_kfs, (uint32_t)h->kfs.size(), seed, h->step, n_rays, b, s); });
+    if (!rc) rc = run_forward(h, n_rays, true, s);
+    if (!rc) rc = phase(h, MAP_PH_COMPOSITE, 1, s, [&] { launch_composite(h->dc, n_rays, true, b, s); });
+    if (!rc)
+        rc = phase(h, MAP_PH_FIELD_BWD, 1, s,
+                   [&] { launch_field_bwd_fp32(h->dc, h->params, h->grads, n_rays, b, h->n_sm, s); });
+    if (rc) return rc;
+    h->last_rays = n_rays;
+    if (!(flags & MAP_STEP_NO_UPDATE)) {
+        const double t = (double)(h->step + 1);
+        const float c1 = (float)(1.0 / (1.0 - std::pow((double)h->cfg.beta1, t)));
+        const float c2 = (float)(1.0 / (1.0 - std::pow((double)h->cfg.beta2, t)));
+        rc = phase(h, MAP_PH_ADAM, 1, s, [&] {
+            launch_adam(h->params, h->grads, h->adam_m, h->adam_v, h->n_params, h->cfg.lr, h->cfg.beta1,
+                        h->cfg.beta2, h->cfg.eps, c1, c2, s);
+        });
+        if (rc) return rc;
+        h->step += 1;
+        if (h->occ_bits && h->cfg.occ_every && h->step % h->cfg.occ_every == 0) {
+            rc = phase(h, MAP_PH_OCC, 1, s, [&] {
+                launch_occ_refresh(h->dc, h->params, h->occ_density, h->occ_bits, h->cfg.seed, h->n_refresh,
+                                   h->cfg.occ_decay, h->cfg.occ_thresh, s);
+            });
+            h->n_refresh += 1;
+            if (rc) return rc;
+        }
+    } else {
+        h->grads_dirty = true;
+    }
+    if (out_loss) return copy_out(h, out_loss, b.loss, sizeof(float), MAP_MEM_HOST, s);
+    return MAP_OK;
+}
+
+const float* map_loss_device(map_handle h) { return h ? h->bufs.loss : nullptr; }
+
+int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, uint32_t H, float* out_rgb,
+               float* out_depth, float* out_acc, int mem_kind, void* stream) {
+    if (!h) return MAP_EINVAL;
+    if (!c2w || !K) return fail(h, MAP_EINVAL, "null camera");
+    if (W == 0 || H == 0 || (uint64_t)W * H > (1u << 24)) return fail(h, MAP_EINVAL, "bad view size");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    const uint32_t n = W * H;
+    int rc = ensure_step_bufs(h, n);
+    if (rc) return rc;
+    const StepBufs& b = h->bufs;
+    rc = phase(h, MAP_PH_RAYGEN, 1, s, [&] { launch_ray_gen_view(c2w, K, W, H, b, s); });
+    if (!rc) rc = run_forward(h, n, false, s);
+    if (rc) return rc;
+    DevCfg dc = h->dc;
+    dc.t_min = h->cfg.render_t_min;
+    rc = phase(h, MAP_PH_COMPOSITE, 1, s, [&] { launch_composite(dc, n, false, b, s); });
+    if (rc) return rc;
+    h->last_rays = n;
+    if (mem_kind == MAP_MEM_DEVICE)
+        return phase(h, MAP_PH_OUTPUT, 1, s, [&] { launch_write_render(b, n, out_rgb, out_depth, out_acc, s); });
+    // host outputs: interleave into the feature buffer (unused by a render), then copy
+    float* tmp = b.feat;
+    rc = phase(h, MAP_PH_OUTPUT, 1, s,
+               [&] { launch_write_render(b, n, tmp, tmp + 3 * (size_t)n, tmp + 4 * (size_t)n, s); });
+    if (rc) return rc;
+    if (out_rgb) NM_CUDA(h, cudaMemcpyAsync(out_rgb, tmp, 3 * (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (out_depth) NM_CUDA(h, cudaMemcpyAsync(out_depth, tmp + 3 * (size_t)n, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (out_acc) NM_CUDA(h, cudaMemcpyAsync(out_acc, tmp + 4 * (size_t)n, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    NM_CUDA(h, cudaStreamSynchronize(s));
+    return MAP_OK;
+}
+
+int map_get_params(map_handle h, float* dst, size_t n, int mem_kind, void* stream) {
+    if (!h || !dst) return MAP_EINVAL;
+    if (n != h->n_params) return fail(h, MAP_EINVAL, "parameter count mismatch");
+    return copy_out(h, dst, h->params, n * sizeof(float), mem_kind, (cudaStream_t)stream);
+}
+
+int map_set_params(map_handle h, const float* src, size_t n, int mem_kind, void* stream) {
+    if (!h || !src) return MAP_EINVAL;
+    if (n != h->n_params) return fail(h, MAP_EINVAL, "parameter count mismatch");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = copy_in(h, h->params, src, n * sizeof(float), mem_kind, s);
+    if (rc) return rc;
+    NM_CUDA(h, cudaStreamSynchronize(s));
+    return MAP_OK;
+}
+
+int map_get_grads(map_handle h, float* dst, size_t n, int mem_kind, void* stream) {
+    if (!h || !dst) return MAP_EINVAL;
+    if (n != h->n_params) return fail(h, MAP_EINVAL, "parameter count mismatch");
+    return copy_out(h, dst, h->grads, n * sizeof(float), mem_kind, (cudaStream_t)stream);
+}
+
+int map_get_adam(map_handle h, float* m, float* v, size_t n, int mem_kind, void* stream) {
+    if (!h) return MAP_EINVAL;
+    if (n != h->n_params) return fail(h, MAP_EINVAL, "parameter count mismatch");
+    int rc = MAP_OK;
+    if (m) rc = copy_out(h, m, h->adam_m, n * sizeof(float), mem_kind, (cudaStream_t)stream);
+    if (!rc && v) rc = copy_out(h, v, h->adam_v, n * sizeof(float), mem_kind, (cudaStream_t)stream);
+    return rc;
+}
+
+int map_reset_adam(map_handle h, void* stream) {
+    if (!h) return MAP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    NM_CUDA(h, cudaMemsetAsync(h->adam_m, 0, h->n_params * sizeof(float), s));
+    NM_CUDA(h, cudaMemsetAsync(h->adam_v, 0, h->n_params * sizeof(float), s));
+    NM_CUDA(h, cudaMemsetAsync(h->grads, 0, h->n_params * sizeof(float), s));
+    h->step = 0;
+    h->grads_dirty = false;
+    return MAP_OK;
+}
+
+int map_set_occupancy(map_handle h, const uint8_t* bits, size_t n_bytes, int mem_kind, void* stream) {
+    if (!h || !bits) return MAP_EINVAL;
+    if (!h->occ_bits) return fail(h, MAP_EINVAL, "map has no occupancy grid");
+    if (n_bytes != h->n_cells / 8) return fail(h, MAP_EINVAL, "occupancy size mismatch");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = copy_in(h, h->occ_bits, bits, n_bytes, mem_kind, s);
+    if (rc) return rc;
+    launch_occ_from_bits(h->occ_bits, h->occ_density, h->n_cells, s);
+    rc = check_launch(h, "occupancy");
+    if (rc) return rc;
+    NM_CUDA(h, cudaStreamSynchronize(s));
+    return MAP_OK;
+}
+
+int map_set_occupancy_density(map_handle h, const float* density, size_t n, int mem_kind, void* stream) {
+    if (!h || !density) return MAP_EINVAL;
+    if (!h->occ_bits) return fail(h, MAP_EINVAL, "map has no occupancy grid");
+    if (n != h->n_cells) return fail(h, MAP_EINVAL, "occupancy size mismatch");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = copy_in(h, h->occ_density, density, n * sizeof(float), mem_kind, s);
+    if (rc) return rc;
+    NM_CUDA(h, cudaStreamSynchronize(s));
+    return MAP_OK;
+}
+
+int map_get_occupancy(map_handle h, uint8_t* bits, float* density, int mem_kind, void* stream) {
+    if (!h) return MAP_EINVAL;
+    if (!h->occ_bits) return fail(h, MAP_EINVAL, "map has no occupancy grid");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = MAP_OK;
+    if (bits) rc = copy_out(h, bits, h->occ_bits, h->n_cells / 8, mem_kind, s);
+    if (!rc && density) rc = copy_out(h, density, h->occ_density, h->n_cells * sizeof(float), mem_kind, s);
+    return rc;
+}
+
+int map_refresh_occupancy(map_handle h, void* stream) {
+    if (!h) return MAP_EINVAL;
+    if (!h->occ_bits) return fail(h, MAP_EINVAL, "map has no occupancy grid");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int rc = phase(h, MAP_PH_OCC, 1, s, [&] {
+        launch_occ_refresh(h->dc, h->params, h->occ_density, h->occ_bits, h->cfg.seed, h->n_refresh,
+                           h->cfg.occ_decay, h->cfg.occ_thresh, s);
+    });
+    h->n_refresh += 1;
+    return rc;
+}
+
+static int last_total(map_scene* h, uint64_t* total) {
+    *total = 0;
+    if (!h->last_rays) return MAP_OK;
+    uint32_t t = 0;
+    int rc = copy_out(h, &t, h->bufs.offsets + h->last_rays, sizeof(uint32_t), MAP_MEM_HOST, h->last_stream);
+    *total = t;
+    return rc;
+}
+
+int map_get_samples(map_handle h, uint32_t* ray_id, float* t, size_t cap, void* stream) {
+    if (!h) return MAP_EINVAL;
+    (void)stream;
+    uint64_t total;
+    int rc = last_total(h, &total);
+    if (rc) return rc;
+    const size_t n = std::min<size_t>(cap, total);
+    if (ray_id && n) rc = copy_out(h, ray_id, h->bufs.ray_id, n * sizeof(uint32_t), MAP_MEM_HOST, h->last_stream);
+    if (!rc && t && n) rc = copy_out(h, t, h->bufs.t, n * sizeof(float), MAP_MEM_HOST, h->last_stream);
+    return rc;
+}
+
+int map_get_ray_outputs(map_handle h, float* rgb, float* depth, float* acc, size_t n_rays, void* stream) {
+    if (!h) return MAP_EINVAL;
+    (void)stream;
+    if (n_rays > h->last_rays) return fail(h, MAP_EINVAL, "more rays than the last step");
+    cudaStream_t s = h->last_stream;
+    const uint32_t cap = h->bufs.cap_rays;
+    int rc = MAP_OK;
+    for (int c = 0; c < 3 && rgb && !rc; ++c) {
+        std::vector<float> tmp(n_rays);
+        rc = copy_out(h, tmp.data(), h->bufs.ray_out + (size_t)c * cap, n_rays * sizeof(float), MAP_MEM_HOST, s);
+        for (size_t i = 0; i < n_rays; ++i) rgb[3 * i + c] = tmp[i];
+    }
+    if (!rc && depth) rc = copy_out(h, depth, h->bufs.ray_out + 3 * (size_t)cap, n_rays * sizeof(float), MAP_MEM_HOST, s);
+    if (!rc && acc) rc = copy_out(h, acc, h->bufs.ray_out + 4 * (size_t)cap, n_rays * sizeof(float), MAP_MEM_HOST, s);
+    return rc;
+}
+
+int map_get_stats(map_handle h, map_stats* out) {
+    if (!h || !out) return MAP_EINVAL;
+    uint64_t total;
+    int rc = last_total(h, &total);
+    if (rc) return rc;
+    out->step = h->step;
+    out->n_samples = total;
+    out->n_rays = h->last_rays;
+    out->n_keyframes = (uint32_t)h->kfs.size();
+    out->param_count = h->n_params;
+    out->device_bytes = h->held;
+    out->kernel_launches = h->launches;
+    return MAP_OK;
+}
+
+int map_profile_enable(map_handle h, int enable) {
+    if (!h) return MAP_EINVAL;
+    if (enable) {
+        cudaDeviceSynchronize();
+        prof_clear(h);
+    }
+    h->prof_on = enable != 0;
+    return MAP_OK;
+}
+
+int map_profile_read(map_handle h, double* ms, uint64_t* count, uint64_t* launches) {
+    if (!h) return MAP_EINVAL;
+    double acc[MAP_PHASES] = {0};
+    uint64_t cnt[MAP_PHASES] = {0}, lch[MAP_PHASES] = {0};
+    for (auto& r : h->prof) {
+        NM_CUDA(h, cudaEventSynchronize(r.b));
+        float t = 0.f;
+        NM_CUDA(h, cudaEventElapsedTime(&t, r.a, r.b));
+        acc[r.phase] += t;
+        cnt[r.phase] += 1;
+        lch[r.phase] += r.launches;
+    }
+    for (int p = 0; p < MAP_PHASES; ++p) {
+        if (ms) ms[p] = acc[p];
+        if (count) count[p] = cnt[p];
+        if (launches) launches[p] = lch[p];
+    }
+    return MAP_OK;
+}
+
+size_t map_abi_config_size(void) { return sizeof(map_config); }
+
+const char* map_last_error(map_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// common.cuh - device-side definitions shared by the mapping kernels.
+//
+// Integer decisions (ray draw, sample positions, box / occupancy tests, grid cells)
+// are taken in IEEE float32 with an explicit operation order: every product and sum
+// on that path uses the _rn intrinsics so the compiler cannot contract it into an
+// FMA.  Everything else may use ordinary FP32 arithmetic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nm {
+
+constexpr int kMaxLevels = 32;
+constexpr int kEnc = 32;       // density-MLP input width (L*F zero padded)
+constexpr int kHid = 64;       // hidden width of both MLPs
+constexpr int kGeo = 16;       // density-MLP output width
+constexpr int kSH = 16;        // SH coefficients, bands 0..3
+constexpr int kW1 = kHid * kEnc;          // 2048
+constexpr int kW2 = kGeo * kHid;          // 1024
+constexpr int kW3 = kHid * (kGeo + kSH);  // 2048
+constexpr int kW4 = kHid * kHid;          // 4096
+constexpr int kW5 = 3 * kHid;             // 192
+constexpr int kMlpParams = kW1 + kW2 + kW3 + kW4 + kW5;  // 9408
+constexpr int kOffW1 = 0, kOffW2 = kW1, kOffW3 = kW1 + kW2, kOffW4 = kOffW3 + kW3,
+              kOffW5 = kOffW4 + kW4;
+
+// Kernel-side copy of the configuration (passed by value).
+struct DevCfg {
+    uint32_t L;
+    uint32_t log2T;
+    uint32_t T;
+    uint32_t dense_mask;          // bit l: level l indexed densely
+    uint32_t res[kMaxLevels];     // N_l
+    float near_t, step_t;
+    uint32_t n_steps, max_samples;
+    float org[3];
+    float inv_size;
+    float box[3];
+    uint32_t occ_res;
+    float lambda_d;
+    float t_min;                  // render early-termination threshold (0: none)
+};
+
+// ----------------------------------------------------------------- exact FP32
+
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// ----------------------------------------------------------------- SplitMix64
+// Published SplitMix64 output function (Steele, Lea & Flood 2014): advance by the
+// golden gamma, then xor-shift 30 / multiply, xor-shift 27 / multiply, xor-shift 31.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Counter-based draw: counter = stream << 33 | index << 1 | k, output = mix(seed ^ ctr).
+__host__ __device__ __forceinline__ uint64_t counter_rand(uint64_t seed, uint64_t stream,
+                                                          uint64_t index, uint64_t k) {
+    return splitmix64(seed ^ ((stream << 33) | (index << 1) | k));
+}
+
+constexpr uint64_t kOccStream = 1ull << 30;
+
+// ----------------------------------------------------------------- geometry
+
+// Grid position of step i of a ray: t = near + i*step, x = (o + t d - org) * inv.
+__device__ __forceinline__ float sample_t(const DevCfg& c, uint32_t i) {
+    return fadd(c.near_t, fmul((float)i, c.step_t));
+}
+
+__device__ __forceinline__ float3 grid_pos(const DevCfg& c, float3 o, float3 d, float t) {
+    float3 x;
+    x.x = fmul(fsub(fadd(o.x, fmul(t, d.x)), c.org[0]), c.inv_size);
+    x.y = fmul(fsub(fadd(o.y, fmul(t, d.y)), c.org[1]), c.inv_size);
+    x.z = fmul(fsub(fadd(o.z, fmul(t, d.z)), c.org[2]), c.inv_size);
+    return x;
+}
+
+__device__ __forceinline__ bool in_box(const DevCfg& c, float3 x) {
+    return x.x >= 0.f && x.y >= 0.f && x.z >= 0.f && x.x < c.box[0] && x.y < c.box[1] &&
+           x.z < c.box[2];
+}
+
+__device__ __forceinline__ int cell_of(float x, uint32_t res) {
+    int ci = (int)floorf(fmul(x, (float)res));
+    ci = ci < 0 ? 0 : ci;
+    return ci > (int)res - 1 ? (int)res - 1 : ci;
+}
+
+__device__ __forceinline__ bool occupied(const DevCfg& c, const uint32_t* __restrict__ bits,
+                                         float3 x) {
+    if (c.occ_res == 0) return true;
+    const uint32_t R = c.occ_res;
+    uint32_t b = (uint32_t)cell_of(x.x, R) + R * ((uint32_t)cell_of(x.y, R) + R * (uint32_t)cell_of(x.z, R));
+    return (__ldg(bits + (b >> 5)) >> (b & 31)) & 1u;
+}
+
+// ----------------------------------------------------------------- hash grid
+
+// Table slot of vertex (cx, cy, cz) at resolution N of a level (dense or hashed).
+__device__ __forceinline__ uint32_t vertex_slot(uint32_t cx, uint32_t cy, uint32_t cz,
+                                                uint32_t N, bool dense, uint32_t Tmask) {
+    if (dense) {
+        const uint32_t s = N + 1;
+        return cx + s * (cy + s * cz);
+    }
+    return (cx ^ (cy * 2654435761u) ^ (cz * 805459861u)) & Tmask;
+}
+
+// Cell and fractional offset at resolution N: q = x*N, c = min(floor q, N-1), w = q - c.
+__device__ __forceinline__ void level_cell(float x, uint32_t N, uint32_t& ci, float& w) {
+    const float q = fmul(x, (float)N);
+    int c = (int)floorf(q);
+    c = c > (int)N - 1 ? (int)N - 1 : c;
+    c = c < 0 ? 0 : c;
+    ci = (uint32_t)c;
+    w = fsub(q, (float)c);
+}
+
+// ----------------------------------------------------------------- SH bands 0..3
+// Real orthonormal spherical harmonics (Condon-Shortley phase); the constants are
+// the Legendre normalisations sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (x sqrt 2, m != 0).
+__device__ __forceinline__ void sh16(float x, float y, float z, float* out) {
+    const float kPi = 3.14159265358979323846f;
+    const float c0 = 0.5f * sqrtf(1.f / kPi);
+    const float c1 = sqrtf(3.f / (4.f * kPi));
+    const float c2a = 0.5f * sqrtf(15.f / kPi);
+    const float c2b = 0.25f * sqrtf(5.f / kPi);
+    const float c2c = 0.25f * sqrtf(15.f / kPi);
+    const float c3a = 0.25f * sqrtf(35.f / (2.f * kPi));
+    const float c3b = 0.5f * sqrtf(105.f / kPi);
+    const float c3c = 0.25f * sqrtf(21.f / (2.f * kPi));
+    const float c3d = 0.25f * sqrtf(7.f / kPi);
+    const float c3e = 0.25f * sqrtf(105.f / kPi);
+    const float xx = x * x, yy = y * y, zz = z * z;
+    out[0] = c0;
+    out[1] = -c1 * y;
+    out[2] = c1 * z;
+    out[3] = -c1 * x;
+    out[4] = c2a * x * y;
+    out[5] = -c2a * y * z;
+    out[6] = c2b * (3.f * zz - 1.f);
+    out[7] = -c2a * x * z;
+    out[8] = c2c * (xx - yy);
+    out[9] = -c3a * y * (3.f * xx - yy);
+    out[10] = c3b * x * y * z;
+    out[11] = -c3c * y * (5.f * zz - 1.f);
+    out[12] = c3d * z * (5.f * zz - 3.f);
+    out[13] = -c3c * x * (5.f * zz - 1.f);
+    out[14] = c3e * z * (xx - yy);
+    out[15] = -c3a * x * (xx - 3.f * yy);
+}
+
+// ----------------------------------------------------------------- error flag
+// Kernels record an out-of-range condition (which they then skip) in a device word
+// the host reads after the step; nothing on the device traps.
+enum : uint32_t { kErrNone = 0, kErrSampleOverflow = 1, kErrBadRay = 2, kErrTimeout = 4 };
+
+}  // namespace nm

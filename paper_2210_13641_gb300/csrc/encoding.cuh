@@ -1,0 +1,82 @@
+// encoding.cuh - multiresolution hash-grid encoding and its gradient scatter
+// (step a3 / a11).  The grid is the Instant-NGP encoding the paper uses as its map
+// (Sec. 3.4): per level l, the sample's cell at resolution N_l, the 8 corner slots
+// (dense index or spatial hash), and trilinear interpolation of 2 FP32 features.
+#pragma once
+
+#include "common.cuh"
+
+namespace nm {
+
+// Trilinear corner weight of corner k = bx + 2 by + 4 bz.
+__device__ __forceinline__ float corner_weight(int k, float wx, float wy, float wz) {
+    return ((k & 1) ? wx : 1.f - wx) * ((k & 2) ? wy : 1.f - wy) * ((k & 4) ? wz : 1.f - wz);
+}
+
+// Encodes grid position x into f[0 .. 2L) (f[2L .. 32) set to zero).
+// tables: [L][T] float2.
+__device__ __forceinline__ void hash_encode(const DevCfg& c, const float2* __restrict__ tables,
+                                            float3 x, float* f) {
+    const uint32_t Tmask = c.T - 1;
+#pragma unroll
+    for (int l = 0; l < kEnc / 2; ++l) {
+        float a0 = 0.f, a1 = 0.f;
+        if (l < (int)c.L) {
+            const uint32_t N = c.res[l];
+            const bool dense = (c.dense_mask >> l) & 1u;
+            uint32_t cx, cy, cz;
+            float wx, wy, wz;
+            level_cell(x.x, N, cx, wx);
+            level_cell(x.y, N, cy, wy);
+            level_cell(x.z, N, cz, wz);
+            const float2* tab = tables + (size_t)l * c.T;
+            float2 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t slot = vertex_slot(cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1),
+                                                  N, dense, Tmask);
+                v[k] = __ldg(tab + slot);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float wk = corner_weight(k, wx, wy, wz);
+                a0 += wk * v[k].x;
+                a1 += wk * v[k].y;
+            }
+        }
+        f[2 * l] = a0;
+        f[2 * l + 1] = a1;
+    }
+}
+
+// dL/dtable[l][slot_k] += w_k * dL/df_l for every corner and level (FP32 atomics,
+// one 8-byte vector reduction per corner).
+__device__ __forceinline__ void hash_scatter(const DevCfg& c, float2* __restrict__ gtables,
+                                             float3 x, const float* df) {
+    const uint32_t Tmask = c.T - 1;
+#pragma unroll
+    for (int l = 0; l < kEnc / 2; ++l) {
+        if (l < (int)c.L) {
+            const uint32_t N = c.res[l];
+            const bool dense = (c.dense_mask >> l) & 1u;
+            uint32_t cx, cy, cz;
+            float wx, wy, wz;
+            level_cell(x.x, N, cx, wx);
+            level_cell(x.y, N, cy, wy);
+            level_cell(x.z, N, cz, wz);
+            float2* gtab = gtables + (size_t)l * c.T;
+            const float g0 = df[2 * l], g1 = df[2 * l + 1];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t slot = vertex_slot(cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1),
+                                                  N, dense, Tmask);
+                const float wk = corner_weight(k, wx, wy, wz);
+                atomicAdd(gtab + slot, make_float2(wk * g0, wk * g1));
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
+
+}  // namespace nm

@@ -1,0 +1,73 @@
+// internal.h - host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace nm {
+
+// One keyframe in the device store.  texels: 8 floats per pixel
+// {r, g, b, D, Sigma_D, 0, 0, 0} (one 32-byte sector), D and Sigma_D in ray units.
+struct KfDesc {
+    float c2w[12];
+    float K[4];
+    uint32_t W, H;
+    const float4* texels;
+};
+
+// Ray batch, structure of arrays: 11 planes of `cap` floats.
+enum RayPlane { kOx = 0, kOy, kOz, kDx, kDy, kDz, kIr, kIg, kIb, kD, kV, kRayPlanes };
+
+struct StepBufs {
+    float* rays;            // [kRayPlanes][cap_rays]
+    uint32_t cap_rays;
+    uint32_t* counts;       // [cap_rays]
+    uint32_t* offsets;      // [cap_rays + 1] exclusive scan, offsets[n] = total
+    uint32_t* block_sums;   // scan scratch
+    uint32_t* ray_id;       // [cap_samples]
+    float* t;               // [cap_samples]
+    float4* sig_rgb;        // [cap_samples] sigma, r, g, b
+    float4* dsig_rgb;       // [cap_samples] dL/dsigma, dL/dr, dL/dg, dL/db (w_i while compositing)
+    float* feat;            // [cap_samples][32] stored encodings (FP32)
+    float* ray_out;         // [5][cap_rays] I*r, I*g, I*b, D*, acc
+    float* loss;            // [1] + partial
+    uint32_t* err;          // [1]
+    uint64_t cap_samples;
+};
+
+// k_rays.cu
+void launch_keyframe_texels(const float* rgb, const float* depth, const float* var, uint32_t W,
+                            uint32_t H, const float* K, int depth_is_z, float4* texels,
+                            cudaStream_t s);
+void launch_ray_gen(const KfDesc* kfs, uint32_t n_kf, uint64_t seed, uint64_t step,
+                    uint32_t n_rays, const StepBufs& b, cudaStream_t s);
+void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t H,
+                         const StepBufs& b, cudaStream_t s);
+void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, const StepBufs& b,
+                  cudaStream_t s);
+
+// k_field_fp32.cu
+void launch_field_fwd_fp32(const DevCfg& c, const float* params, uint32_t n_rays,
+                           const StepBufs& b, bool store_feat, int n_sm, cudaStream_t s);
+void launch_field_bwd_fp32(const DevCfg& c, const float* params, float* grads, uint32_t n_rays,
+                           const StepBufs& b, int n_sm, cudaStream_t s);
+
+// k_composite.cu
+void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const StepBufs& b,
+                      cudaStream_t s);
+void launch_write_render(const StepBufs& b, uint32_t n, float* rgb, float* depth, float* acc,
+                         cudaStream_t s);
+
+// k_adam_occ.cu
+void launch_adam(float* p, float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
+                 float eps, float c1, float c2, cudaStream_t s);
+void launch_init_params(float* p, size_t n_table, uint64_t seed, cudaStream_t s);
+void launch_occ_refresh(const DevCfg& c, const float* params, float* density, uint32_t* bits,
+                        uint64_t seed, uint64_t refresh_idx, float decay, float thresh,
+                        cudaStream_t s);
+void launch_occ_from_bits(const uint32_t* bits, float* density, uint32_t n_cells, cudaStream_t s);
+
+}  // namespace nm

@@ -1,0 +1,239 @@
+// k_rays.cu - keyframe texels, ray generation, march with occupancy test, and the
+// exclusive scan that compacts the retained samples (steps a1-a2 of the mapping
+// step; sampling follows Sec. 3.2 of the paper, the ray draw Sec. 3.3).
+#include "internal.h"
+
+namespace nm {
+
+// ---------------------------------------------------------------- keyframe texels
+// Converts a keyframe to the store's texel layout.  z-depth is turned into distance
+// along the unit ray: D = z * s, Sigma_D = var * s^2, s = ||K^-1 [u+1/2, v+1/2, 1]||.
+__global__ void k_keyframe_texels(const float* __restrict__ rgb, const float* __restrict__ depth,
+                                  const float* __restrict__ var, uint32_t W, uint32_t H,
+                                  float fx, float fy, float cx, float cy, int depth_is_z,
+                                  float4* __restrict__ tex) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= W * H) return;
+    const uint32_t u = p % W, v = p / W;
+    float D = depth[p], V = var[p];
+    if (depth_is_z) {
+        const float sx = ((float)u + 0.5f - cx) / fx;
+        const float sy = ((float)v + 0.5f - cy) / fy;
+        const float s2 = sx * sx + sy * sy + 1.f;
+        D *= sqrtf(s2);
+        V *= s2;
+    }
+    tex[2 * p] = make_float4(rgb[3 * p], rgb[3 * p + 1], rgb[3 * p + 2], D);
+    tex[2 * p + 1] = make_float4(V, 0.f, 0.f, 0.f);
+}
+
+void launch_keyframe_texels(const float* rgb, const float* depth, const float* var, uint32_t W,
+                            uint32_t H, const float* K, int depth_is_z, float4* texels,
+                            cudaStream_t s) {
+    const uint32_t n = W * H;
+    k_keyframe_texels<<<(n + 255) / 256, 256, 0, s>>>(rgb, depth, var, W, H, K[0], K[1], K[2],
+                                                       K[3], depth_is_z, texels);
+}
+
+// ---------------------------------------------------------------- ray casting
+// Back-projection of the pixel centre, rotation to world, normalisation; exact
+// FP32 operation order (the same integer decisions follow from these values).
+__device__ __forceinline__ void cast_ray(const float* c2w, const float* K, uint32_t u,
+                                         uint32_t v, float3& o, float3& d) {
+    const float dx = fdiv(fsub(fadd((float)u, 0.5f), K[2]), K[0]);
+    const float dy = fdiv(fsub(fadd((float)v, 0.5f), K[3]), K[1]);
+    const float wx = fadd(fadd(fmul(c2w[0], dx), fmul(c2w[1], dy)), c2w[2]);
+    const float wy = fadd(fadd(fmul(c2w[4], dx), fmul(c2w[5], dy)), c2w[6]);
+    const float wz = fadd(fadd(fmul(c2w[8], dx), fmul(c2w[9], dy)), c2w[10]);
+    const float n = __fsqrt_rn(fadd(fadd(fmul(wx, wx), fmul(wy, wy)), fmul(wz, wz)));
+    d = make_float3(fdiv(wx, n), fdiv(wy, n), fdiv(wz, n));
+    o = make_float3(c2w[3], c2w[7], c2w[11]);
+}
+
+__device__ __forceinline__ void store_ray(float* rays, uint32_t cap, uint32_t r, float3 o,
+                                          float3 d, float4 t0, float V) {
+    rays[kOx * cap + r] = o.x;
+    rays[kOy * cap + r] = o.y;
+    rays[kOz * cap + r] = o.z;
+    rays[kDx * cap + r] = d.x;
+    rays[kDy * cap + r] = d.y;
+    rays[kDz * cap + r] = d.z;
+    rays[kIr * cap + r] = t0.x;
+    rays[kIg * cap + r] = t0.y;
+    rays[kIb * cap + r] = t0.z;
+    rays[kD * cap + r] = t0.w;
+    rays[kV * cap + r] = V;
+}
+
+// Uniform draw with replacement over (keyframe, pixel): keyframe = r0 mod n_kf,
+// pixel = r1 mod (W*H), with r0, r1 the two counter draws of the ray.
+__global__ void k_ray_gen(const KfDesc* __restrict__ kfs, uint32_t n_kf, uint64_t seed,
+                          uint64_t step, uint32_t n_rays, float* __restrict__ rays, uint32_t cap) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const uint64_t r0 = counter_rand(seed, step, r, 0);
+    const uint64_t r1 = counter_rand(seed, step, r, 1);
+    const KfDesc& kf = kfs[r0 % n_kf];
+    const uint64_t pix = r1 % ((uint64_t)kf.W * kf.H);
+    const uint32_t u = (uint32_t)(pix % kf.W), v = (uint32_t)(pix / kf.W);
+    float3 o, d;
+    cast_ray(kf.c2w, kf.K, u, v, o, d);
+    const float4 t0 = __ldg(kf.texels + 2 * pix);
+    const float4 t1 = __ldg(kf.texels + 2 * pix + 1);
+    store_ray(rays, cap, r, o, d, t0, t1.x);
+}
+
+void launch_ray_gen(const KfDesc* kfs, uint32_t n_kf, uint64_t seed, uint64_t step,
+                    uint32_t n_rays, const StepBufs& b, cudaStream_t s) {
+    k_ray_gen<<<(n_rays + 255) / 256, 256, 0, s>>>(kfs, n_kf, seed, step, n_rays, b.rays,
+                                                   b.cap_rays);
+}
+
+struct ViewCam {
+    float c2w[12];
+    float K[4];
+};
+
+__global__ void k_ray_gen_view(ViewCam cam, uint32_t W, uint32_t H, float* __restrict__ rays,
+                               uint32_t cap) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= W * H) return;
+    float3 o, d;
+    cast_ray(cam.c2w, cam.K, r % W, r / W, o, d);
+    store_ray(rays, cap, r, o, d, make_float4(0.f, 0.f, 0.f, 0.f), 1.f);
+}
+
+void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t H,
+                         const StepBufs& b, cudaStream_t s) {
+    ViewCam cam;
+    for (int i = 0; i < 12; ++i) cam.c2w[i] = c2w[i];
+    for (int i = 0; i < 4; ++i) cam.K[i] = K[i];
+    const uint32_t n = W * H;
+    k_ray_gen_view<<<(n + 255) / 256, 256, 0, s>>>(cam, W, H, b.rays, b.cap_rays);
+}
+
+// ---------------------------------------------------------------- march
+// Pass 1 counts the retained steps of each ray, pass 2 (after the scan) writes
+// (ray, t) of each retained step at the ray's offset, in step order.
+template <bool kEmit>
+__global__ void k_march(DevCfg c, const uint32_t* __restrict__ bits, uint32_t n_rays,
+                        const float* __restrict__ rays, uint32_t cap, uint32_t* __restrict__ counts,
+                        const uint32_t* __restrict__ offsets, uint32_t* __restrict__ ray_id,
+                        float* __restrict__ ts) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const float3 o = make_float3(rays[kOx * cap + r], rays[kOy * cap + r], rays[kOz * cap + r]);
+    const float3 d = make_float3(rays[kDx * cap + r], rays[kDy * cap + r], rays[kDz * cap + r]);
+    uint32_t n = 0;
+    const uint32_t base = kEmit ? offsets[r] : 0;
+    for (uint32_t i = 0; i < c.n_steps && n < c.max_samples; ++i) {
+        const float t = sample_t(c, i);
+        const float3 x = grid_pos(c, o, d, t);
+        if (!in_box(c, x) || !occupied(c, bits, x)) continue;
+        if (kEmit) {
+            ray_id[base + n] = r;
+            ts[base + n] = t;
+        }
+        ++n;
+    }
+    if (!kEmit) counts[r] = n;
+}
+
+// Exclusive scan of counts[0..n) into offsets[0..n], offsets[n] = total.
+// Level 1: each 1024-thread block scans 4096 entries and writes its block total.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
+                                                         uint32_t& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    total = warp_tot[(blockDim.x >> 5) - 1];
+    const uint32_t before = wid > 0 ? warp_tot[wid - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t* __restrict__ in,
+                                                              uint32_t n, uint32_t* __restrict__ out,
+                                                              uint32_t* __restrict__ tile_sums) {
+    __shared__ uint32_t warp_tot[32];
+    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    uint32_t v[kScanPer];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(s, warp_tot, total);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Level 2: one block scans the tile totals (at most kScanTile of them) in place.
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t* __restrict__ tile_sums,
+                                                            uint32_t n_tiles,
+                                                            uint32_t* __restrict__ total_out) {
+    __shared__ uint32_t warp_tot[32];
+    const uint32_t base = threadIdx.x * kScanPer;
+    uint32_t v[kScanPer];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = (base + k < n_tiles) ? tile_sums[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(s, warp_tot, total);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n_tiles) tile_sums[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) *total_out = total;
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, uint32_t n,
+                           const uint32_t* __restrict__ tile_sums) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tile_sums[i / kScanTile];
+}
+
+void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, const StepBufs& b,
+                  cudaStream_t s) {
+    const uint32_t grid = (n_rays + 127) / 128;
+    k_march<false><<<grid, 128, 0, s>>>(c, occ_bits, n_rays, b.rays, b.cap_rays, b.counts,
+                                        nullptr, nullptr, nullptr);
+    const uint32_t n_tiles = (n_rays + kScanTile - 1) / kScanTile;  // <= kScanTile (n <= 2^24)
+    k_scan_tiles<<<n_tiles, kScanThreads, 0, s>>>(b.counts, n_rays, b.offsets, b.block_sums);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(b.block_sums, n_tiles, b.offsets + n_rays);
+    k_scan_add<<<(n_rays + 255) / 256, 256, 0, s>>>(b.offsets, n_rays, b.block_sums);
+    k_march<true><<<grid, 128, 0, s>>>(c, occ_bits, n_rays, b.rays, b.cap_rays, nullptr,
+                                       b.offsets, b.ray_id, b.t);
+}
+
+}  // namespace nm

@@ -72,29 +72,38 @@ def _intersect(room: Room, o: np.ndarray, d: np.ndarray):
     t_best = tw[np.arange(n), axis]
     side = (d[np.arange(n), axis] > 0).astype(np.int64)
     obj = axis * 2 + side
-    for i in range(len(room.sph_r)):
-        oc = o - room.sph_c[i]
-        a = np.sum(d * d, axis=1)
-        b = np.sum(d * oc, axis=1)
-        c = np.sum(oc * oc, axis=1) - room.sph_r[i] ** 2
-        disc = b * b - a * c
-        ok = disc >= 0
-        t = np.where(ok, (-b - np.sqrt(np.where(ok, disc, 0))) / a, np.inf)
-        hit = ok & (t > 1e-6) & (t < t_best)
-        t_best = np.where(hit, t, t_best)
-        obj = np.where(hit, 6 + i, obj)
+    a = np.sum(d * d, axis=1)
+    CH = 65536
     ns = len(room.sph_r)
-    for i in range(len(room.box_h)):
-        lo = room.box_c[i] - room.box_h[i]
-        hi = room.box_c[i] + room.box_h[i]
+    for s0 in range(0, n, CH):                     # chunks keep the [chunk, prims, 3] arrays small
+        sl = slice(s0, min(n, s0 + CH))
+        oc = o[sl, None, :] - room.sph_c[None]     # [c, ns, 3]
+        b = np.einsum("ca,cpa->cp", d[sl], oc)
+        cc = np.sum(oc * oc, axis=2) - room.sph_r[None] ** 2
+        disc = b * b - a[sl, None] * cc
+        ok = disc >= 0
+        t = np.where(ok, (-b - np.sqrt(np.where(ok, disc, 0))) / a[sl, None], np.inf)
+        t = np.where(t > 1e-6, t, np.inf)
+        if ns:
+            i = np.argmin(t, axis=1)
+            tm = t[np.arange(t.shape[0]), i]
+            hit = tm < t_best[sl]
+            t_best[sl] = np.where(hit, tm, t_best[sl])
+            obj[sl] = np.where(hit, 6 + i, obj[sl])
+        lo = room.box_c - room.box_h
+        hi = room.box_c + room.box_h
         with np.errstate(divide="ignore", invalid="ignore"):
-            a0 = (lo - o) * inv
-            a1 = (hi - o) * inv
-        tn = np.max(np.minimum(a0, a1), axis=1)
-        tf = np.min(np.maximum(a0, a1), axis=1)
-        hit = (tn <= tf) & (tn > 1e-6) & (tn < t_best)
-        t_best = np.where(hit, tn, t_best)
-        obj = np.where(hit, 6 + ns + i, obj)
+            a0 = (lo[None] - o[sl, None, :]) * inv[sl, None, :]
+            a1 = (hi[None] - o[sl, None, :]) * inv[sl, None, :]
+        tn = np.max(np.minimum(a0, a1), axis=2)
+        tf = np.min(np.maximum(a0, a1), axis=2)
+        tn = np.where((tn <= tf) & (tn > 1e-6), tn, np.inf)
+        if len(room.box_h):
+            i = np.argmin(tn, axis=1)
+            tm = tn[np.arange(tn.shape[0]), i]
+            hit = tm < t_best[sl]
+            t_best[sl] = np.where(hit, tm, t_best[sl])
+            obj[sl] = np.where(hit, 6 + ns + i, obj[sl])
     return t_best, obj
 
 

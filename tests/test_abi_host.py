@@ -1,0 +1,95 @@
+"""Host-side checks (no GPU): the library builds, loads and exports every symbol the
+header declares; configuration marshalling and parameter packing are consistent with
+the oracle's own definitions."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "nerfmap.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(map_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2210_13641_gb300 import binding
+    return binding.load()
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    from paper_2210_13641_gb300 import binding
+    names = _header_functions()
+    assert len(names) >= 20
+    raw = ctypes.CDLL(binding.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+    assert sorted(binding.exported_symbols()) == names
+
+
+def test_config_struct_layout(lib):
+    from paper_2210_13641_gb300 import binding
+    assert lib.map_abi_config_size() == ctypes.sizeof(binding.MapConfig)
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    """Without a device map_create returns an error code with a message (no crash)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2210_13641_gb300 import MapError, NerfMap
+    with pytest.raises(MapError):
+        NerfMap(synth.config_small())
+
+
+def test_invalid_configs_rejected_before_device_use(lib):
+    from paper_2210_13641_gb300 import binding
+    for bad in (dict(n_levels=0), dict(log2_table=30), dict(max_samples=0), dict(occ_res=12)):
+        c = binding.make_config(synth.config_small().replace(**{k: v for k, v in bad.items() if k != "n_levels"}))
+        if "n_levels" in bad:
+            c.n_levels = 0
+        h = ctypes.c_void_p()
+        rc = lib.map_create(ctypes.byref(c), 0, ctypes.byref(h))
+        assert rc == binding.MAP_EINVAL, bad
+        assert lib.map_last_error(None)
+
+
+@pytest.mark.parametrize("mk", [synth.config_small, synth.config_c1, synth.config_c2, synth.config_c5])
+def test_level_table_matches_oracle(mk):
+    from paper_2210_13641_gb300 import binding
+    cfg = mk()
+    assert binding.level_resolutions(cfg.n_levels, cfg.n_min, cfg.growth, cfg.n_max) == \
+        oracle.level_resolutions(cfg)
+
+
+def test_pack_unpack_roundtrip():
+    from paper_2210_13641_gb300 import pack_params, unpack_params
+    cfg = synth.config_small()
+    P = synth.random_params(cfg, 1)
+    flat = pack_params(P)
+    assert flat.size == cfg.n_levels * cfg.table_size * 2 + 9408
+    Q = unpack_params(flat, cfg.n_levels, cfg.log2_table)
+    for k in P:
+        assert np.array_equal(P[k], Q[k])
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2210_13641_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f
+                assert "oracle/" not in txt, f

@@ -1,0 +1,240 @@
+"""Parity of the CUDA mapping path (through the C ABI) with the FP64 oracle.
+
+Tolerances (plain FP32 form): sample lists and occupancy bits bit-exact; loss and
+per-ray renders within 1e-5 relative; each gradient tensor within 1e-5 relative in
+L2 norm and element-wise within 1e-5 relative plus an absolute floor of 1e-6 of the
+tensor's largest magnitude (FP32 atomics sum thousands of terms per table entry in
+an arbitrary order, so an entry whose terms cancel carries an absolute, not a
+relative, rounding error of that size).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    torch.cuda.init()
+    yield
+
+
+def _map(cfg, P, kfs, occ_bits=None):
+    from paper_2210_13641_gb300 import NerfMap, pack_params
+    m = NerfMap(cfg, occ_every=0)
+    m.set_params(pack_params(P))
+    for kf in kfs:
+        m.add_keyframe(kf)
+    if occ_bits is not None:
+        m.set_occupancy(occ_bits)
+    return m
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _check_grads(g_gpu, g_ref, rel=REL, floor=1e-6):
+    for k in ("tables", "W1", "W2", "W3", "W4", "W5"):
+        a = np.asarray(g_gpu[k], np.float64)
+        b = g_ref[k]
+        assert _rel(a, b) <= rel, (k, _rel(a, b))
+        tol = rel * np.abs(b) + floor * np.abs(b).max()
+        bad = np.abs(a - b) > tol
+        assert not bad.any(), (k, int(bad.sum()), float(np.abs(a - b)[bad].max()))
+
+
+def _check_step(m, ref, n_rays, loss):
+    rid, t = m.samples()
+    assert np.array_equal(rid, ref["ray_id"].astype(np.uint32))
+    assert np.array_equal(t.view(np.uint32), ref["t"].astype(np.float32).view(np.uint32))
+    assert loss == pytest.approx(ref["loss"], rel=REL)
+    rgb, D, acc = m.ray_outputs(n_rays)
+    assert np.allclose(rgb, ref["I_hat"], rtol=REL, atol=1e-6)
+    assert np.allclose(D, ref["D_hat"], rtol=REL, atol=1e-6)
+    assert np.allclose(acc, ref["acc"], rtol=REL, atol=1e-6)
+
+
+def test_c1_step_parity_fp32():
+    cfg = synth.config_c1()
+    P = synth.random_params(cfg, 0)
+    kf = synth.c1_keyframe(0)
+    m = _map(cfg, P, [kf])
+    loss = m.step(4096, seed=7, no_update=True)
+    ref = oracle.forward_backward(cfg, P, [kf], 4096, 7, 0)
+    _check_step(m, ref, 4096, loss)
+    _check_grads(m.unpack(m.get_grads()), ref["grads"])
+
+
+def test_small_multi_keyframe_occupancy_truncation_ragged():
+    """Two dense and two hashed levels, a random 16^3 bitfield, at most 16 samples
+    per ray (truncation), three keyframes of different sizes with z-depth, and a
+    ray count that is not a multiple of any tile."""
+    cfg = synth.config_small(occ_res=16)
+    P = synth.random_params(cfg, 3, table_scale=0.05, mlp_std=0.2)
+    rng = np.random.default_rng(4)
+    kfs = []
+    for j, (W, H) in enumerate([(40, 30), (23, 17), (64, 9)]):
+        kf = synth.c1_keyframe(10 + j, W=W, H=H, kf_id=100 + j)
+        kf.depth_is_z = True
+        kfs.append(kf)
+    bits = np.packbits(rng.uniform(size=16 ** 3) < 0.6, bitorder="little")
+    m = _map(cfg, P, kfs, bits)
+    n = 3001
+    loss = m.step(n, seed=11, no_update=True)
+    ref = oracle.forward_backward(cfg, P, kfs, n, 11, 0, occ_bits=bits)
+    assert np.bincount(ref["ray_id"], minlength=n).max() == cfg.max_samples
+    _check_step(m, ref, n, loss)
+    _check_grads(m.unpack(m.get_grads()), ref["grads"])
+
+
+def test_adam_update_and_step_counter():
+    cfg = synth.config_small(occ_res=0)
+    P = synth.random_params(cfg, 5, table_scale=0.05, mlp_std=0.2)
+    kf = synth.c1_keyframe(6, W=32, H=24)
+    m = _map(cfg, P, [kf])
+    m.step(1000, seed=3, no_update=True)
+    G = m.unpack(m.get_grads().copy())
+    m.step(1000, seed=3)                      # same draw (step index 0), now with Adam
+    newP = m.unpack(m.get_params())
+    mm, vv = m.get_adam()
+    z = {k: np.zeros_like(v, dtype=np.float64) for k, v in P.items()}
+    refP, refM, refV = oracle.adam_update(P, G, z, z, 1, cfg)
+    for k in P:
+        assert np.allclose(newP[k], refP[k], rtol=1e-6, atol=1e-9), k
+    assert np.allclose(m.unpack(mm)["W4"], refM["W4"], rtol=1e-6, atol=1e-12)
+    assert np.allclose(m.unpack(vv)["tables"], refV["tables"], rtol=1e-5, atol=1e-20)
+    assert m.stats().step == 1
+    # the next draw uses step index 1
+    m.step(1000, seed=3, no_update=True)
+    rid, t = m.samples()
+    kfi, u, v = oracle.draw_rays(3, 1, 1000, [(kf.W, kf.H)])
+    o, d = oracle.cast_rays_f32(np.broadcast_to(kf.c2w, (1000, 3, 4)), np.broadcast_to(kf.K, (1000, 4)), u, v)
+    r_ref, _, t_ref, _ = oracle.march(cfg, o, d)
+    assert np.array_equal(rid, r_ref) and np.array_equal(t, t_ref)
+
+
+def test_render_parity_with_early_termination():
+    cfg = synth.config_small(occ_res=0, render_t_min=np.float32(1e-2))
+    P = synth.random_params(cfg, 8, table_scale=0.5, mlp_std=0.3)
+    P["W2"][0] += 0.3                          # denser field: rays terminate early
+    m = _map(cfg, P, [synth.c1_keyframe(0, W=8, H=8)])
+    kf = synth.c1_keyframe(9, W=48, H=36)
+    rgb, D, acc = m.render(kf.c2w, kf.K, 48, 36)
+    I_ref, D_ref, A_ref = oracle.render(cfg, P, kf.c2w, kf.K, 48, 36, t_min=1e-2)
+    assert np.mean(A_ref > 0.9) > 0.2
+    assert np.allclose(rgb.reshape(-1, 3), I_ref, rtol=REL, atol=1e-6)
+    assert np.allclose(D.ravel(), D_ref, rtol=REL, atol=1e-6)
+    assert np.allclose(acc.ravel(), A_ref, rtol=REL, atol=1e-6)
+
+
+def test_render_device_buffers_match_host():
+    import torch
+    cfg = synth.config_c1()
+    P = synth.random_params(cfg, 1)
+    m = _map(cfg, P, [synth.c1_keyframe(0)])
+    kf = synth.c1_keyframe(2)
+    rgb_h, d_h, a_h = m.render(kf.c2w, kf.K, 64, 48)
+    out = torch.zeros((48, 64, 3), device="cuda")
+    dep = torch.zeros((48, 64), device="cuda")
+    m.render(kf.c2w, kf.K, 64, 48, out_rgb=out, out_depth=dep)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), rgb_h) and np.array_equal(dep.cpu().numpy(), d_h)
+
+
+def test_occupancy_refresh_parity():
+    cfg = synth.config_small(occ_res=16)
+    P = synth.random_params(cfg, 12, table_scale=1.0, mlp_std=0.3)
+    m = _map(cfg, P, [synth.c1_keyframe(0, W=8, H=8)])
+    dens0 = np.random.default_rng(13).uniform(0, 0.03, 16 ** 3).astype(np.float32)
+    m.set_occupancy_density(dens0)
+    m.refresh_occupancy()
+    m.refresh_occupancy()
+    bits, dens = m.get_occupancy()
+    d1, _, _ = oracle.occupancy_refresh(cfg, P, dens0.astype(np.float64), 0, cfg.seed)
+    d2, bits_ref, _ = oracle.occupancy_refresh(cfg, P, d1, 1, cfg.seed)
+    assert np.allclose(dens, d2, rtol=REL, atol=0)
+    near = np.abs(d2 - float(cfg.occ_thresh)) < 1e-4 * float(cfg.occ_thresh)
+    b_gpu = np.unpackbits(bits, bitorder="little").astype(bool)
+    b_ref = np.unpackbits(bits_ref, bitorder="little").astype(bool)
+    assert np.array_equal(b_gpu[~near], b_ref[~near])
+    assert 0.05 < b_ref.mean() < 0.95
+
+
+def test_edge_cases():
+    from paper_2210_13641_gb300 import MapError, NerfMap
+    cfg = synth.config_c1()
+    P = synth.random_params(cfg, 2)
+    m = NerfMap(cfg, occ_every=0)
+    with pytest.raises(MapError) as e:
+        m.step(16, seed=0)
+    assert e.value.code == -3                  # no keyframes
+    m.set_params(P if isinstance(P, np.ndarray) else __import__("paper_2210_13641_gb300").pack_params(P))
+    # camera outside the box looking away: no ray has a sample
+    kf = synth.c1_keyframe(3)
+    kf.c2w = synth.look_at_pose([3.0, 3.0, 3.0], [6.0, 6.0, 6.0])
+    m.add_keyframe(kf)
+    loss = m.step(100, seed=1, no_update=True)
+    ref = oracle.forward_backward(cfg, P, [kf], 100, 1, 0)
+    assert len(ref["t"]) == 0 and m.stats().n_samples == 0
+    assert loss == pytest.approx(ref["loss"], rel=REL)
+    assert not np.any(m.get_grads())
+    with pytest.raises(MapError):
+        m.step(0, seed=1)
+    # replacing the keyframe by id changes what the next step sees
+    kf2 = synth.c1_keyframe(4)
+    kf2.kf_id = kf.kf_id
+    m.add_keyframe(kf2)
+    assert m.stats().n_keyframes == 1
+    loss = m.step(1, seed=5, no_update=True)
+    ref = oracle.forward_backward(cfg, P, [kf2], 1, 5, 0)
+    assert loss == pytest.approx(ref["loss"], rel=REL)
+
+
+@pytest.fixture(scope="module")
+def room_workload():
+    cfg = synth.config_c2(precision="fp32")
+    room = synth.make_room(0)
+    kfs = synth.room_keyframes(room, 20, seed=1)
+    bits = synth.room_occupancy_bits(room, cfg.occ_res, cfg.grid_origin, cfg.grid_inv_size)
+    P = synth.random_params(cfg, 0)
+    return cfg, kfs, bits, P
+
+
+def test_full_size_room_step_sampled(room_workload):
+    """2^18 rays over 20 keyframes of 640x480 at L=16, T=2^19 with the 128^3
+    bitfield (the benchmark's workload): the sample lists of 512 sampled rays are
+    bit-exact, their renders and loss terms match the oracle, and the batch loss
+    equals the mean of the per-ray terms."""
+    cfg, kfs, bits, P = room_workload
+    n = 1 << 18
+    m = _map(cfg, P, kfs, bits)
+    loss = m.step(n, seed=21, no_update=True)
+    rid, t = m.samples()
+    rgb, D, acc = m.ray_outputs(n)
+    kf, u, v = oracle.draw_rays(21, 0, n, [(k.W, k.H) for k in kfs])
+    pick = np.sort(np.random.default_rng(22).choice(n, 512, replace=False))
+    sub = (kf[pick], u[pick], v[pick])
+    ref = oracle.forward_backward(cfg, P, kfs, 512, 0, 0, occ_bits=bits, rays=sub, want_grad=False)
+    starts = np.searchsorted(rid, np.arange(n + 1))
+    counts = np.diff(starts)
+    assert np.array_equal(counts[pick], np.bincount(ref["ray_id"], minlength=512))
+    t_gpu = np.concatenate([t[starts[r]:starts[r + 1]] for r in pick])
+    assert np.array_equal(t_gpu, ref["t"])
+    assert np.allclose(rgb[pick], ref["I_hat"], rtol=REL, atol=1e-6)
+    assert np.allclose(D[pick], ref["D_hat"], rtol=REL, atol=1e-6)
+    # whole-batch loss from the per-ray renders, targets taken by the oracle's draw
+    I, Dt, V = oracle.ray_targets(kf, u, v, kfs)
+    per_ray = ((I - rgb) ** 2).sum(1) + float(cfg.lambda_d) * (Dt - D) ** 2 / V
+    assert loss == pytest.approx(per_ray.mean(), rel=REL)
+    assert counts.mean() > 5
