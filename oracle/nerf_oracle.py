@@ -282,25 +282,63 @@ def relu(a):
     return np.maximum(a, 0.0)
 
 
-def field_forward(P: dict, feat: np.ndarray, sh: np.ndarray) -> dict:
+def round_to(x, precision):
+    """Round to the MLP operand type: IEEE binary16 (saturating at +-65504) or
+    bfloat16 (round to nearest even of the float32 value); None: unchanged."""
+    x = np.asarray(x, np.float64)
+    if precision is None or precision == "fp32":
+        return x
+    if precision == "fp16":
+        return np.clip(x, -65504.0, 65504.0).astype(np.float16).astype(np.float64)
+    if precision == "bf16":
+        b = x.astype(np.float32).view(np.uint32).astype(np.uint64)
+        b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+        return b.astype(np.uint32).view(np.float32).astype(np.float64)
+    raise ValueError(precision)
+
+
+FP16_FEATURE_SCALE = 256.0   # FP16 encodings enter the MLP as fp16(2^8 f)
+
+
+def relu_decisions(P: dict, feat: np.ndarray, sh: np.ndarray, precision: str):
+    """The ReLU branch of every hidden unit as the FP16/BF16 MLP takes it: the same
+    layer chain on operands rounded to the MLP type (products summed exactly).  A
+    ReLU branch is an integer decided by floating point, so parity takes it in the
+    kernel's precision; the values themselves stay FP64 (field_forward)."""
+    R = lambda a: round_to(a, precision)
+    W = {k: R(P[k]) for k in ("W1", "W2", "W3", "W4", "W5")}
+    fs = FP16_FEATURE_SCALE if precision == "fp16" else 1.0
+    a1 = R(feat * fs) @ W["W1"].T / fs
+    h = R(relu(a1)) @ W["W2"].T
+    a3 = R(np.concatenate([h, sh], axis=1)) @ W["W3"].T
+    a4 = R(relu(a3)) @ W["W4"].T
+    return a1 > 0, a3 > 0, a4 > 0
+
+
+def field_forward(P: dict, feat: np.ndarray, sh: np.ndarray, decisions=None) -> dict:
     """sigma_i and c_i from one evaluation of the MLPs at the sample (Sec. 3.2: both
     are estimated simultaneously).  Density MLP: h = W2 relu(W1 feat), sigma =
     exp(h_0).  Colour MLP on [h; SH]: c = sigmoid(W5 relu(W4 relu(W3 [h; SH]))).
-    No biases.  Returns every intermediate (for the backward pass)."""
+    No biases.  `decisions` (from relu_decisions) fixes the ReLU branches; by
+    default each unit is active when its FP64 pre-activation is positive.
+    Returns every intermediate (for the backward pass)."""
     W = {k: P[k].astype(np.float64) for k in ("W1", "W2", "W3", "W4", "W5")}
     a1 = feat @ W["W1"].T
-    h1 = relu(a1)
+    m1 = a1 > 0 if decisions is None else decisions[0]
+    h1 = np.where(m1, a1, 0.0)
     h = h1 @ W["W2"].T
     sigma = np.exp(h[:, 0])
     x3 = np.concatenate([h, sh], axis=1)
     a3 = x3 @ W["W3"].T
-    h3 = relu(a3)
+    m3 = a3 > 0 if decisions is None else decisions[1]
+    h3 = np.where(m3, a3, 0.0)
     a4 = h3 @ W["W4"].T
-    h4 = relu(a4)
+    m4 = a4 > 0 if decisions is None else decisions[2]
+    h4 = np.where(m4, a4, 0.0)
     z = h4 @ W["W5"].T
     rgb = 1.0 / (1.0 + np.exp(-z))
-    return dict(feat=feat, a1=a1, h1=h1, h=h, sigma=sigma, x3=x3, a3=a3, h3=h3,
-                a4=a4, h4=h4, z=z, rgb=rgb)
+    return dict(feat=feat, a1=a1, m1=m1, h1=h1, h=h, sigma=sigma, x3=x3, a3=a3, m3=m3, h3=h3,
+                a4=a4, m4=m4, h4=h4, z=z, rgb=rgb)
 
 
 # ------------------------------------------------------------------ a7: compositing
@@ -367,26 +405,53 @@ def composite_backward_ray(sigma, rgb, t, delta, w, Tcum, gI, gD):
     return dsig, drgb
 
 
+def composite_backward_ray_abs(sigma, rgb, t, delta, w, Tcum, gI, gD):
+    """Sum of the absolute values of the terms of composite_backward_ray (every
+    term is w, T, c, t >= 0 times |g|): the scale of that sum's rounding error."""
+    T_next = Tcum * np.exp(-sigma * delta)
+    wc = w[:, None] * rgb
+    wt = w * t
+    suf_c = np.cumsum(wc[::-1], axis=0)[::-1] - wc
+    suf_t = np.cumsum(wt[::-1])[::-1] - wt
+    dsig = delta * ((T_next[:, None] * rgb + suf_c) @ np.abs(gI) + abs(gD) * (T_next * t + suf_t))
+    drgb = w[:, None] * np.abs(gI)[None, :]
+    return dsig, drgb
+
+
 # ------------------------------------------------------------------ a10, a11: backward
 
-def field_backward(P: dict, fw: dict, dsigma, drgb):
-    """Chain rule through the MLPs (a10).  Returns weight gradients and dL/dfeat."""
+def field_backward(P: dict, fw: dict, dsigma, drgb, magnitude: bool = False):
+    """Chain rule through the MLPs (a10).  Returns weight gradients and dL/dfeat.
+    magnitude=True (with the absolute-term inputs of composite_backward_ray_abs)
+    runs the same chain on |W| and on activation magnitudes (each activation
+    replaced by the sum of the absolute values of its own terms, same ReLU
+    branches): every output is then the sum of the absolute values of the products
+    that make up the matching gradient entry, expanded down to the inputs - the
+    scale of its rounding error in any summation order."""
     W = {k: P[k].astype(np.float64) for k in ("W1", "W2", "W3", "W4", "W5")}
+    if magnitude:
+        W = {k: np.abs(v) for k, v in W.items()}
+        f = np.abs(fw["feat"])
+        h1 = np.where(fw["m1"], f @ W["W1"].T, 0.0)
+        x3 = np.concatenate([h1 @ W["W2"].T, np.abs(fw["x3"][:, P["W2"].shape[0]:])], axis=1)
+        h3 = np.where(fw["m3"], x3 @ W["W3"].T, 0.0)
+        h4 = np.where(fw["m4"], h3 @ W["W4"].T, 0.0)
+        fw = dict(fw, feat=f, h1=h1, x3=x3, h3=h3, h4=h4)
     rgb = fw["rgb"]
     dz = drgb * rgb * (1.0 - rgb)
     g = {"W5": dz.T @ fw["h4"]}
     dh4 = dz @ W["W5"]
-    da4 = dh4 * (fw["a4"] > 0)
+    da4 = dh4 * fw["m4"]
     g["W4"] = da4.T @ fw["h3"]
     dh3 = da4 @ W["W4"]
-    da3 = dh3 * (fw["a3"] > 0)
+    da3 = dh3 * fw["m3"]
     g["W3"] = da3.T @ fw["x3"]
     dx3 = da3 @ W["W3"]
     dh = dx3[:, :P["W2"].shape[0]].copy()
     dh[:, 0] += dsigma * fw["sigma"]
     g["W2"] = dh.T @ fw["h1"]
     dh1 = dh @ W["W2"]
-    da1 = dh1 * (fw["a1"] > 0)
+    da1 = dh1 * fw["m1"]
     g["W1"] = da1.T @ fw["feat"]
     dfeat = da1 @ W["W1"]
     return g, dfeat
@@ -406,9 +471,13 @@ def hash_backward(cfg, idx, wts, dfeat):
 # ------------------------------------------------------------------ the step
 
 def forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits=None,
-                     level_res=None, rays=None, want_grad=True):
+                     level_res=None, rays=None, want_grad=True, magnitudes=False,
+                     decide_in=None):
     """a1-a11: loss L_M and its gradient for one batch.  Returns a dict with the
-    loss, per-ray renders, the sample list and the named gradients."""
+    loss, per-ray renders, the sample list and the named gradients; with
+    magnitudes=True also `grads_abs`, per entry the sum of the absolute values of
+    the products that form it (see field_backward).  decide_in = "fp16" | "bf16"
+    takes the ReLU branches in that MLP precision (relu_decisions)."""
     level_res = level_resolutions(cfg) if level_res is None else level_res
     if rays is None:
         kf, u, v = draw_rays(seed, step, n_rays, [(k.W, k.H) for k in keyframes])
@@ -421,7 +490,8 @@ def forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits=None,
     ray_id, step_idx, t, x = march(cfg, o, d, occ_bits)
     feat, idx, wts = hash_encode(cfg, level_res, P["tables"], x)
     sh = sh_deg4(d[ray_id])
-    fw = field_forward(P, feat, sh)
+    dec = relu_decisions(P, feat, sh, decide_in) if decide_in not in (None, "fp32") else None
+    fw = field_forward(P, feat, sh, dec)
     delta = float(cfg.step)
     t64 = t.astype(np.float64)
     I_hat, D_hat, acc, w, Tcum = composite(ray_id, fw["sigma"], fw["rgb"], t64, delta, n_rays)
@@ -446,6 +516,20 @@ def forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits=None,
     g, dfeat = field_backward(P, fw, dsig, drgb)
     g["tables"] = hash_backward(cfg, idx, wts, dfeat)
     out.update(grads=g, dsigma=dsig, drgb=drgb, dfeat=dfeat)
+    if magnitudes:
+        dsa = np.zeros(len(t))
+        dra = np.zeros((len(t), 3))
+        gIa = 2.0 * (np.abs(I) + np.abs(I_hat)) / n_rays          # residual I - I*: two terms
+        gDa = 2.0 * lam * (np.abs(D) + np.abs(D_hat)) / (V * n_rays)
+        for r in range(n_rays):
+            a, b = starts[r], starts[r + 1]
+            if a == b:
+                continue
+            dsa[a:b], dra[a:b] = composite_backward_ray_abs(
+                fw["sigma"][a:b], fw["rgb"][a:b], t64[a:b], delta, w[a:b], Tcum[a:b], gIa[r], gDa[r])
+        ga, dfa = field_backward(P, fw, dsa, dra, magnitude=True)
+        ga["tables"] = hash_backward(cfg, idx, wts, dfa)
+        out["grads_abs"] = ga
     return out
 
 
@@ -508,7 +592,7 @@ def render_rays_f32(c2w, K, W, H):
     return o, d
 
 
-def render(cfg, P, c2w, K, W, H, occ_bits=None, level_res=None, t_min=None):
+def render(cfg, P, c2w, K, W, H, occ_bits=None, level_res=None, t_min=None, decide_in=None):
     """Forward-only render of a W x H view (PAPER Sec. 3.3, the mapping thread also
     renders): colour [H*W, 3] and expected depth [H*W]; with t_min, samples after
     the transmittance drops below t_min are skipped."""
@@ -516,7 +600,9 @@ def render(cfg, P, c2w, K, W, H, occ_bits=None, level_res=None, t_min=None):
     o, d = render_rays_f32(np.asarray(c2w, f32), np.asarray(K, f32), W, H)
     ray_id, _, t, x = march(cfg, o, d, occ_bits)
     feat, _, _ = hash_encode(cfg, level_res, P["tables"], x)
-    fw = field_forward(P, feat, sh_deg4(d[ray_id]))
+    sh = sh_deg4(d[ray_id])
+    dec = relu_decisions(P, feat, sh, decide_in) if decide_in not in (None, "fp32") else None
+    fw = field_forward(P, feat, sh, dec)
     I_hat, D_hat, acc, _, _ = composite(ray_id, fw["sigma"], fw["rgb"], t.astype(np.float64),
                                         float(cfg.step), W * H, t_min)
     return I_hat, D_hat, acc

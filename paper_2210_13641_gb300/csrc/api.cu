@@ -209,6 +209,18 @@ int copy_out(map_scene* h, void* dst, const void* src, size_t bytes, int mem_kin
     return MAP_OK;
 }
 
+// Error word the kernels set instead of trapping (a bounded wait that expired).
+int check_device_flags(map_scene* h, cudaStream_t s) {
+    uint32_t e = 0;
+    NM_CUDA(h, cudaMemcpyAsync(&e, h->bufs.err, sizeof(e), cudaMemcpyDeviceToHost, s));
+    NM_CUDA(h, cudaStreamSynchronize(s));
+    if (e & kErrTimeout) {
+        cudaMemsetAsync(h->bufs.err, 0, sizeof(uint32_t), s);
+        return fail(h, MAP_ETIMEOUT, "a tensor-core wait expired on the device");
+    }
+    return MAP_OK;
+}
+
 int check_launch(map_scene* h, const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, what);
@@ -388,8 +400,12 @@ static int run_forward(map_scene* h, uint32_t n_rays, bool train, cudaStream_t s
     const StepBufs& b = h->bufs;
     int rc = phase(h, MAP_PH_MARCH, 5, s, [&] { launch_march(h->dc, h->occ_bits, n_rays, b, s); });
     if (rc) return rc;
-    return phase(h, MAP_PH_FIELD_FWD, 1, s,
-                 [&] { launch_field_fwd_fp32(h->dc, h->params, n_rays, b, train, h->n_sm, s); });
+    return phase(h, MAP_PH_FIELD_FWD, 1, s, [&] {
+        if (h->cfg.precision == MAP_PREC_FP32)
+            launch_field_fwd_fp32(h->dc, h->params, n_rays, b, train, h->n_sm, s);
+        else
+            launch_field_fwd_tc(h->dc, h->params, n_rays, b, train, h->cfg.precision == MAP_PREC_BF16, h->n_sm, s);
+    });
 }
 
 int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float* out_loss, void* stream) {
@@ -410,8 +426,13 @@ int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float
     if (!rc) rc = run_forward(h, n_rays, true, s);
     if (!rc) rc = phase(h, MAP_PH_COMPOSITE, 1, s, [&] { launch_composite(h->dc, n_rays, true, b, s); });
     if (!rc)
-        rc = phase(h, MAP_PH_FIELD_BWD, 1, s,
-                   [&] { launch_field_bwd_fp32(h->dc, h->params, h->grads, n_rays, b, h->n_sm, s); });
+        rc = phase(h, MAP_PH_FIELD_BWD, 1, s, [&] {
+            if (h->cfg.precision == MAP_PREC_FP32)
+                launch_field_bwd_fp32(h->dc, h->params, h->grads, n_rays, b, h->n_sm, s);
+            else
+                launch_field_bwd_tc(h->dc, h->params, h->grads, n_rays, b, h->cfg.precision == MAP_PREC_BF16,
+                                    h->n_sm, s);
+        });
     if (rc) return rc;
     h->last_rays = n_rays;
     if (!(flags & MAP_STEP_NO_UPDATE)) {
@@ -435,7 +456,11 @@ int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float
     } else {
         h->grads_dirty = true;
     }
-    if (out_loss) return copy_out(h, out_loss, b.loss, sizeof(float), MAP_MEM_HOST, s);
+    if (out_loss) {
+        rc = copy_out(h, out_loss, b.loss, sizeof(float), MAP_MEM_HOST, s);
+        if (rc) return rc;
+        return check_device_flags(h, s);
+    }
     return MAP_OK;
 }
 

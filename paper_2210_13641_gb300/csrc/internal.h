@@ -55,6 +55,12 @@ void launch_field_fwd_fp32(const DevCfg& c, const float* params, uint32_t n_rays
 void launch_field_bwd_fp32(const DevCfg& c, const float* params, float* grads, uint32_t n_rays,
                            const StepBufs& b, int n_sm, cudaStream_t s);
 
+// k_field_tc.cu (FP16 / BF16 tensor-core MLP)
+void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b,
+                         bool store_feat, bool bf16, int n_sm, cudaStream_t s);
+void launch_field_bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t n_rays,
+                         const StepBufs& b, bool bf16, int n_sm, cudaStream_t s);
+
 // k_composite.cu
 void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const StepBufs& b,
                       cudaStream_t s);

@@ -1,0 +1,582 @@
+// k_field_tc.cu - the field on the 5th-generation tensor cores (FP16 or BF16
+// operands, FP32 accumulation in tensor memory): hash encoding, density MLP
+// (sigma = exp(h_0)), SH view encoding and colour MLP forward (steps a3-a6), and the
+// recomputing backward pass with the weight gradients accumulated in tensor memory
+// across a persistent block's tiles (steps a10-a11).
+//
+// A block owns a tile of 128 samples at a time; thread r of the block owns sample
+// row r, which is TMEM lane r of every 128-row accumulator.  Each layer is one
+// chain of tcgen05.mma instructions issued by thread 0 on shared-memory operands
+// (layout in tc_ptx.cuh), committed to an mbarrier; the block then reads the
+// accumulator rows back with tcgen05.ld, applies the activation in FP32, rounds to
+// the MLP type and writes the next operand tile.  Weight gradients are M=64
+// products over the tile's samples (MN-major operands of the same tiles) that keep
+// accumulating in TMEM until the block has no tiles left.
+//
+// Gradient tiles are scaled by a power of two S before rounding to the MLP type:
+// S brings the step's largest per-sample gradient seed to about 2^13, which keeps
+// the small seeds out of FP16's subnormal range and leaves headroom below 65504.
+// FP16 encodings enter the MLP scaled by 2^8 (table values start near 1e-4, below
+// FP16's normal range).  Both scales are exact and are removed in FP32.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "encoding.cuh"
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace nm {
+
+using namespace tc;
+
+namespace {
+
+constexpr uint32_t kWaitPolls = 1u << 24;
+
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    if constexpr (BF16) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&v);
+    } else {
+        a = fminf(fmaxf(a, -65504.f), 65504.f);
+        b = fminf(fmaxf(b, -65504.f), 65504.f);
+        __half2 v = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&v);
+    }
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint16_t pack1(float a) {
+    if constexpr (BF16) {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(a));
+    } else {
+        return __half_as_ushort(__float2half_rn(fminf(fmaxf(a, -65504.f), 65504.f)));
+    }
+}
+
+// Row r (of 128) of a tile with C columns, from C floats.
+template <bool BF16, int C>
+__device__ __forceinline__ void store_row(uint8_t* tile, int r, const float* v) {
+#pragma unroll
+    for (int g = 0; g < C / 8; ++g) {
+        uint4 q;
+        q.x = pack2<BF16>(v[8 * g + 0], v[8 * g + 1]);
+        q.y = pack2<BF16>(v[8 * g + 2], v[8 * g + 3]);
+        q.z = pack2<BF16>(v[8 * g + 4], v[8 * g + 5]);
+        q.w = pack2<BF16>(v[8 * g + 6], v[8 * g + 7]);
+        *reinterpret_cast<uint4*>(tile + tile_offset(r, 8 * g, 128)) = q;
+    }
+}
+
+// N consecutive accumulator columns of this thread's lane.
+template <int N>
+__device__ __forceinline__ void ld_cols(uint32_t trow, uint32_t col, float* v) {
+#pragma unroll
+    for (int c = 0; c < N; c += 16) tmem_ld16(trow + col + c, v + c);
+    tmem_wait_ld();
+}
+
+struct Op {
+    uint32_t addr, lbo, sbo, kstep;
+};
+// Tile with R rows used as a K-major operand (rows = M or N, columns = K).
+__device__ __forceinline__ Op kmaj(const void* t, int R) {
+    return Op{smem_u32(t), (uint32_t)(R / 8) * 128u, 128u, (uint32_t)(R / 8) * 256u};
+}
+// Tile with R rows used as an MN-major operand (rows = K, columns = M or N).
+__device__ __forceinline__ Op mnmaj(const void* t, int R) {
+    return Op{smem_u32(t), 128u, (uint32_t)(R / 8) * 128u, 256u};
+}
+
+__device__ __forceinline__ void gemm(uint32_t d, Op a, Op b, int ksteps, uint32_t idesc, bool acc) {
+    for (int k = 0; k < ksteps; ++k)
+        mma_f16(d, smem_desc(a.addr + k * a.kstep, a.lbo, a.sbo), smem_desc(b.addr + k * b.kstep, b.lbo, b.sbo),
+                idesc, (acc || k > 0) ? 1u : 0u);
+}
+
+// Makes this thread's operand writes visible to the tensor core and orders its
+// earlier TMEM reads before the next MMA; block-wide.
+__device__ __forceinline__ void to_tensor() {
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+}
+
+// Waits for the MMAs committed to `bar` (bounded); after a timeout the thread stops
+// waiting for the rest of the tile and the block leaves at the tile's end.
+__device__ __forceinline__ void wait_mma(uint64_t* bar, uint32_t& phase, bool& timed_out) {
+    if (!timed_out) timed_out = !mbar_wait(bar, phase, kWaitPolls);
+    phase ^= 1u;
+    fence_after_sync();
+}
+
+// Weight tiles (MLP type) from the FP32 master weights: W1 64x32, W2 16x64,
+// W3 64x32, W4 64x64, W5 padded to 16x64 (rows 3..15 zero).
+template <bool BF16>
+__device__ void load_weight_tiles(const float* __restrict__ mlp, uint8_t* sW1, uint8_t* sW2, uint8_t* sW3,
+                                  uint8_t* sW4, uint8_t* sW5) {
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
+        const float w = mlp[i];
+        uint8_t* dst;
+        if (i < kOffW2) {
+            dst = sW1 + tile_offset(i / 32, i % 32, 64);
+        } else if (i < kOffW3) {
+            const int j = i - kOffW2;
+            dst = sW2 + tile_offset(j / 64, j % 64, 16);
+        } else if (i < kOffW4) {
+            const int j = i - kOffW3;
+            dst = sW3 + tile_offset(j / 32, j % 32, 64);
+        } else if (i < kOffW5) {
+            const int j = i - kOffW4;
+            dst = sW4 + tile_offset(j / 64, j % 64, 64);
+        } else {
+            const int j = i - kOffW5;
+            dst = sW5 + tile_offset(j / 64, j % 64, 16);
+        }
+        *reinterpret_cast<uint16_t*>(dst) = pack1<BF16>(w);
+    }
+    for (int j = 192 + threadIdx.x; j < 16 * 64; j += blockDim.x)
+        *reinterpret_cast<uint16_t*>(sW5 + tile_offset(j / 64, j % 64, 16)) = 0;
+}
+
+__device__ __forceinline__ float3 sample_pos_tc(const DevCfg& c, const float* __restrict__ rays, uint32_t cap,
+                                                uint32_t r, float t, float3& d) {
+    const float3 o = make_float3(rays[kOx * cap + r], rays[kOy * cap + r], rays[kOz * cap + r]);
+    d = make_float3(rays[kDx * cap + r], rays[kDy * cap + r], rays[kDz * cap + r]);
+    return grid_pos(c, o, d, t);
+}
+
+constexpr int kW1B = 64 * 32 * 2, kW2B = 16 * 64 * 2, kW3B = 64 * 32 * 2, kW4B = 64 * 64 * 2, kW5B = 16 * 64 * 2;
+constexpr int kWB = kW1B + kW2B + kW3B + kW4B + kW5B;  // 20480
+constexpr int kT32 = 128 * 32 * 2, kT64 = 128 * 64 * 2, kT16 = 128 * 16 * 2;
+
+}  // namespace
+
+constexpr int kFwdSmem = kWB + kT32 + kT64 + kT64;                     // 61440
+constexpr int kBwdSmem = kWB + kT32 + kT64 + kT32 + kT64 + kT64 + kT16;  // 90112
+
+// ------------------------------------------------------------------ forward
+template <bool BF16>
+__global__ void __launch_bounds__(128) k_field_fwd_tc(DevCfg c, const float* __restrict__ params,
+                                                      const float* __restrict__ rays, uint32_t cap,
+                                                      const uint32_t* __restrict__ n_total,
+                                                      const uint32_t* __restrict__ ray_id,
+                                                      const float* __restrict__ ts, float4* __restrict__ sig_rgb,
+                                                      uint4* __restrict__ feat_out, float feat_scale,
+                                                      uint32_t* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    uint8_t* sW1 = smem;
+    uint8_t* sW2 = sW1 + kW1B;
+    uint8_t* sW3 = sW2 + kW2B;
+    uint8_t* sW4 = sW3 + kW3B;
+    uint8_t* sW5 = sW4 + kW4B;
+    uint8_t* tA = smem + kWB;   // X0, X3   (128 x 32)
+    uint8_t* tB = tA + kT32;    // H1, H3   (128 x 64)
+    uint8_t* tC = tB + kT64;    // H4       (128 x 64)
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    load_weight_tiles<BF16>(params + (size_t)c.L * c.T * 2, sW1, sW2, sW3, sW4, sW5);
+    if (warp == 0) tmem_alloc(&tslot, 64);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    to_tensor();
+    const uint32_t tmem = tslot;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t n = *n_total;
+    const uint32_t n_tiles = (n + 127) / 128;
+    const float2* tables = reinterpret_cast<const float2*>(params);
+    const float inv_fs = 1.f / feat_scale;
+    uint32_t phase = 0;
+    bool timed_out = false;
+
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint32_t i = tile * 128 + tid;
+        const bool valid = i < n;
+        float v[64];
+        float3 d = make_float3(0.f, 0.f, 0.f);
+        if (valid) {
+            const float3 x = sample_pos_tc(c, rays, cap, ray_id[i], ts[i], d);
+            hash_encode(c, tables, x, v);
+#pragma unroll
+            for (int k = 0; k < kEnc; ++k) v[k] *= feat_scale;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kEnc; ++k) v[k] = 0.f;
+        }
+        store_row<BF16, 32>(tA, tid, v);
+        if (feat_out && valid) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                feat_out[(size_t)i * 4 + g] = *reinterpret_cast<const uint4*>(tA + tile_offset(tid, 8 * g, 128));
+        }
+        // layer 1: D = X0 W1^T (128 x 64)
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tA, 128), kmaj(sW1, 64), 2, idesc_f16(128, 64, BF16, false, false), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<64>(trow, 0, v);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = fmaxf(v[k] * inv_fs, 0.f);
+        store_row<BF16, 64>(tB, tid, v);
+        // layer 2: y = H1 W2^T (128 x 16)
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tB, 128), kmaj(sW2, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<16>(trow, 0, v);
+        const float sigma = expf(v[0]);
+        if (valid) sh16(d.x, d.y, d.z, v + kGeo);
+        else {
+#pragma unroll
+            for (int k = kGeo; k < 32; ++k) v[k] = 0.f;
+        }
+        store_row<BF16, 32>(tA, tid, v);
+        // layer 3: H3 = relu(X3 W3^T)
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tA, 128), kmaj(sW3, 64), 2, idesc_f16(128, 64, BF16, false, false), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<64>(trow, 0, v);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = fmaxf(v[k], 0.f);
+        store_row<BF16, 64>(tB, tid, v);
+        // layer 4: H4 = relu(H3 W4^T)
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tB, 128), kmaj(sW4, 64), 4, idesc_f16(128, 64, BF16, false, false), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<64>(trow, 0, v);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = fmaxf(v[k], 0.f);
+        store_row<BF16, 64>(tC, tid, v);
+        // layer 5: z = H4 W5^T (3 of 16 columns used)
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tC, 128), kmaj(sW5, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<16>(trow, 0, v);
+        if (valid) sig_rgb[i] = make_float4(sigma, sigmoidf_(v[0]), sigmoidf_(v[1]), sigmoidf_(v[2]));
+        fence_before_sync();
+        if (__syncthreads_or(timed_out)) {
+            if (tid == 0) atomicOr(err, kErrTimeout);
+            break;
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (timed_out) mbar_wait(&bar, phase ^ 1u, kWaitPolls);
+    if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+// ------------------------------------------------------------------ backward
+// TMEM columns: [0,64) layer chain, [64,128) dW4, [128,160) dW3, [160,192) dW1,
+// [192,208) dW2^T, [208,224) dW5^T.  The weight gradients are M=64 products: row m
+// of such an accumulator is TMEM lane 32*(m/16) + m%16.
+constexpr uint32_t kColW4 = 64, kColW3 = 128, kColW1 = 160, kColW2T = 192, kColW5T = 208;
+
+template <bool BF16>
+__global__ void __launch_bounds__(128) k_field_bwd_tc(DevCfg c, const float* __restrict__ params,
+                                                      float* __restrict__ grads, const float* __restrict__ rays,
+                                                      uint32_t cap, const uint32_t* __restrict__ n_total,
+                                                      const uint32_t* __restrict__ ray_id,
+                                                      const float* __restrict__ ts, const uint4* __restrict__ feat,
+                                                      const float4* __restrict__ dsig_rgb, float feat_scale,
+                                                      const float* __restrict__ seed_max, uint32_t* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    uint8_t* sW1 = smem;
+    uint8_t* sW2 = sW1 + kW1B;
+    uint8_t* sW3 = sW2 + kW2B;
+    uint8_t* sW4 = sW3 + kW3B;
+    uint8_t* sW5 = sW4 + kW4B;
+    uint8_t* tX0 = smem + kWB;   // 128 x 32
+    uint8_t* tH1 = tX0 + kT32;   // 128 x 64  (later G1)
+    uint8_t* tX3 = tH1 + kT64;   // 128 x 32  (later G2 in columns 0..15)
+    uint8_t* tH3 = tX3 + kT32;   // 128 x 64  (later G3)
+    uint8_t* tH4 = tH3 + kT64;   // 128 x 64  (later G4)
+    uint8_t* tG5 = tH4 + kT64;   // 128 x 16
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    load_weight_tiles<BF16>(params + (size_t)c.L * c.T * 2, sW1, sW2, sW3, sW4, sW5);
+    if (warp == 0) tmem_alloc(&tslot, 256);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    to_tensor();
+    const uint32_t tmem = tslot;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t n = *n_total;
+    const uint32_t n_tiles = (n + 127) / 128;
+    float2* gtables = reinterpret_cast<float2*>(grads);
+    const float inv_fs = 1.f / feat_scale;
+    const float gm = seed_max[1];
+    const float S = gm > 0.f ? exp2f(fminf(fmaxf(floorf(log2f(8192.f / gm)), -100.f), 100.f)) : 1.f;
+    const float inv_S = 1.f / S;
+    uint32_t phase = 0;
+    bool timed_out = false;
+    bool first = true;
+    constexpr uint32_t kM128N64 = idesc_f16(128, 64, BF16, false, false);
+    constexpr uint32_t kM128N16 = idesc_f16(128, 16, BF16, false, false);
+
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint32_t i = tile * 128 + tid;
+        const bool valid = i < n;
+        float v[64];
+        float3 x = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 0.f);
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            x = sample_pos_tc(c, rays, cap, ray_id[i], ts[i], d);
+            g = dsig_rgb[i];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4*>(tX0 + tile_offset(tid, 8 * q, 128)) = feat[(size_t)i * 4 + q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4*>(tX0 + tile_offset(tid, 8 * q, 128)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        // ---- forward recompute (same arithmetic as the forward kernel)
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tX0, 128), kmaj(sW1, 64), 2, kM128N64, false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<64>(trow, 0, v);
+        uint32_t m1a = 0, m1b = 0, m3a = 0, m3b = 0, m4a = 0, m4b = 0;
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            const float a = v[k] * inv_fs;
+            if (a > 0.f) {
+                if (k < 32) m1a |= 1u << k;
+                else m1b |= 1u << (k - 32);
+            }
+            v[k] = fmaxf(a, 0.f);
+        }
+        store_row<BF16, 64>(tH1, tid, v);
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tH1, 128), kmaj(sW2, 16), 4, kM128N16, false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<16>(trow, 0, v);
+        const float sigma = expf(v[0]);
+        if (valid) sh16(d.x, d.y, d.z, v + kGeo);
+        else {
+#pragma unroll
+            for (int k = kGeo; k < 32; ++k) v[k] = 0.f;
+        }
+        store_row<BF16, 32>(tX3, tid, v);
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tX3, 128), kmaj(sW3, 64), 2, kM128N64, false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<64>(trow, 0, v);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            if (v[k] > 0.f) {
+                if (k < 32) m3a |= 1u << k;
+                else m3b |= 1u << (k - 32);
+            }
+            v[k] = fmaxf(v[k], 0.f);
+        }
+        store_row<BF16, 64>(tH3, tid, v);
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tH3, 128), kmaj(sW4, 64), 4, kM128N64, false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<64>(trow, 0, v);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            if (v[k] > 0.f) {
+                if (k < 32) m4a |= 1u << k;
+                else m4b |= 1u << (k - 32);
+            }
+            v[k] = fmaxf(v[k], 0.f);
+        }
+        store_row<BF16, 64>(tH4, tid, v);
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem, kmaj(tH4, 128), kmaj(sW5, 16), 4, kM128N16, false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<16>(trow, 0, v);
+        {
+            const float c0 = sigmoidf_(v[0]), c1 = sigmoidf_(v[1]), c2 = sigmoidf_(v[2]);
+            v[0] = S * g.y * c0 * (1.f - c0);
+            v[1] = S * g.z * c1 * (1.f - c1);
+            v[2] = S * g.w * c2 * (1.f - c2);
+#pragma unroll
+            for (int k = 3; k < 16; ++k) v[k] = 0.f;
+        }
+        store_row<BF16, 16>(tG5, tid, v);
+        // ---- backward: dW5^T += H4^T G5 ; dH4 = G5 W5
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem + kColW5T, mnmaj(tH4, 128), mnmaj(tG5, 128), 8, idesc_f16(64, 16, BF16, true, true), !first);
+            gemm(tmem, kmaj(tG5, 128), mnmaj(sW5, 16), 1, idesc_f16(128, 64, BF16, false, true), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<64>(trow, 0, v);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = ((k < 32 ? (m4a >> k) : (m4b >> (k - 32))) & 1u) ? v[k] : 0.f;
+        store_row<BF16, 64>(tH4, tid, v);                       // G4
+        // dW4 += G4^T H3 ; dH3 = G4 W4
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem + kColW4, mnmaj(tH4, 128), mnmaj(tH3, 128), 8, idesc_f16(64, 64, BF16, true, true), !first);
+            gemm(tmem, kmaj(tH4, 128), mnmaj(sW4, 64), 4, idesc_f16(128, 64, BF16, false, true), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<64>(trow, 0, v);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = ((k < 32 ? (m3a >> k) : (m3b >> (k - 32))) & 1u) ? v[k] : 0.f;
+        store_row<BF16, 64>(tH3, tid, v);                       // G3
+        // dW3 += G3^T X3 ; dX3 = G3 W3
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem + kColW3, mnmaj(tH3, 128), mnmaj(tX3, 128), 8, idesc_f16(64, 32, BF16, true, true), !first);
+            gemm(tmem, kmaj(tH3, 128), mnmaj(sW3, 64), 4, idesc_f16(128, 32, BF16, false, true), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<16>(trow, 0, v);
+        v[0] += S * g.x * sigma;                                // dL/dh_0 += dL/dsigma * sigma
+        store_row<BF16, 16>(tX3, tid, v);                       // G2 (columns 0..15)
+        // dW2^T += H1^T G2 ; dH1 = G2 W2
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem + kColW2T, mnmaj(tH1, 128), mnmaj(tX3, 128), 8, idesc_f16(64, 16, BF16, true, true), !first);
+            gemm(tmem, kmaj(tX3, 128), mnmaj(sW2, 16), 1, idesc_f16(128, 64, BF16, false, true), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<64>(trow, 0, v);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = ((k < 32 ? (m1a >> k) : (m1b >> (k - 32))) & 1u) ? v[k] : 0.f;
+        store_row<BF16, 64>(tH1, tid, v);                       // G1
+        // dW1 += G1^T X0 ; dF = G1 W1
+        to_tensor();
+        if (tid == 0) {
+            gemm(tmem + kColW1, mnmaj(tH1, 128), mnmaj(tX0, 128), 8, idesc_f16(64, 32, BF16, true, true), !first);
+            gemm(tmem, kmaj(tH1, 128), mnmaj(sW1, 64), 4, idesc_f16(128, 32, BF16, false, true), false);
+            mma_commit(&bar);
+        }
+        wait_mma(&bar, phase, timed_out);
+        ld_cols<32>(trow, 0, v);
+        if (valid && !timed_out) {
+#pragma unroll
+            for (int k = 0; k < kEnc; ++k) v[k] *= inv_S;
+            hash_scatter(c, gtables, x, v);
+        }
+        first = false;
+        fence_before_sync();
+        if (__syncthreads_or(timed_out)) {
+            if (tid == 0) atomicOr(err, kErrTimeout);
+            break;
+        }
+    }
+    fence_before_sync();
+    const bool any_timeout = __syncthreads_or(timed_out);
+    fence_after_sync();
+    if (timed_out) mbar_wait(&bar, phase ^ 1u, kWaitPolls);
+    // ---- flush the weight gradients (lane 32*(m/16) + m%16 holds row m)
+    if (!first && !any_timeout) {
+        float* gm = grads + (size_t)c.L * c.T * 2;
+        const int lane = tid & 31;
+        const int m = warp * 16 + lane;
+        const bool has = lane < 16;
+        float w[64];
+        ld_cols<64>(trow, kColW4, w);
+        if (has)
+            for (int k = 0; k < 64; ++k) atomicAdd(gm + kOffW4 + m * 64 + k, w[k] * inv_S);
+        ld_cols<32>(trow, kColW3, w);
+        if (has)
+            for (int k = 0; k < 32; ++k) atomicAdd(gm + kOffW3 + m * 32 + k, w[k] * inv_S);
+        ld_cols<32>(trow, kColW1, w);
+        if (has)
+            for (int k = 0; k < 32; ++k) atomicAdd(gm + kOffW1 + m * 32 + k, w[k] * inv_S * inv_fs);
+        ld_cols<16>(trow, kColW2T, w);
+        if (has)
+            for (int k = 0; k < 16; ++k) atomicAdd(gm + kOffW2 + k * 64 + m, w[k] * inv_S);
+        ld_cols<16>(trow, kColW5T, w);
+        if (has)
+            for (int k = 0; k < 3; ++k) atomicAdd(gm + kOffW5 + k * 64 + m, w[k] * inv_S);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <bool BF16>
+static void fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b, bool store_feat,
+                   int n_sm, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_field_fwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+        attr = true;
+    }
+    const float fs = BF16 ? 1.f : 256.f;
+    k_field_fwd_tc<BF16><<<n_sm * 3, 128, kFwdSmem, s>>>(c, params, b.rays, b.cap_rays, b.offsets + n_rays,
+                                                          b.ray_id, b.t, b.sig_rgb,
+                                                          store_feat ? reinterpret_cast<uint4*>(b.feat) : nullptr,
+                                                          fs, b.err);
+}
+
+template <bool BF16>
+static void bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t n_rays, const StepBufs& b, int n_sm,
+                   cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_field_bwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem);
+        attr = true;
+    }
+    const float fs = BF16 ? 1.f : 256.f;
+    k_field_bwd_tc<BF16><<<n_sm * 2, 128, kBwdSmem, s>>>(c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays,
+                                                          b.ray_id, b.t, reinterpret_cast<const uint4*>(b.feat),
+                                                          b.dsig_rgb, fs, b.loss, b.err);
+}
+
+void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b, bool store_feat,
+                         bool bf16, int n_sm, cudaStream_t s) {
+    if (bf16) fwd_tc<true>(c, params, n_rays, b, store_feat, n_sm, s);
+    else fwd_tc<false>(c, params, n_rays, b, store_feat, n_sm, s);
+}
+
+void launch_field_bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t n_rays, const StepBufs& b,
+                         bool bf16, int n_sm, cudaStream_t s) {
+    if (bf16) bwd_tc<true>(c, params, grads, n_rays, b, n_sm, s);
+    else bwd_tc<false>(c, params, grads, n_rays, b, n_sm, s);
+}
+
+}  // namespace nm

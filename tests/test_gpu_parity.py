@@ -2,10 +2,10 @@
 
 Tolerances (plain FP32 form): sample lists and occupancy bits bit-exact; loss and
 per-ray renders within 1e-5 relative; each gradient tensor within 1e-5 relative in
-L2 norm and element-wise within 1e-5 relative plus an absolute floor of 1e-6 of the
-tensor's largest magnitude (FP32 atomics sum thousands of terms per table entry in
-an arbitrary order, so an entry whose terms cancel carries an absolute, not a
-relative, rounding error of that size).
+L2 norm, and each entry within 1e-5 of the sum of the absolute values of the
+products that form it (the oracle's `grads_abs`).  An entry is a sum of thousands
+of products accumulated in FP32 in an arbitrary (atomic) order, so its rounding
+error scales with that absolute sum, not with the entry itself when terms cancel.
 """
 
 import numpy as np
@@ -44,14 +44,14 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _check_grads(g_gpu, g_ref, rel=REL, floor=1e-6):
+def _check_grads(g_gpu, ref, rel=REL, elem=REL):
     for k in ("tables", "W1", "W2", "W3", "W4", "W5"):
         a = np.asarray(g_gpu[k], np.float64)
-        b = g_ref[k]
+        b = ref["grads"][k]
         assert _rel(a, b) <= rel, (k, _rel(a, b))
-        tol = rel * np.abs(b) + floor * np.abs(b).max()
+        tol = elem * ref["grads_abs"][k] + 1e-30
         bad = np.abs(a - b) > tol
-        assert not bad.any(), (k, int(bad.sum()), float(np.abs(a - b)[bad].max()))
+        assert not bad.any(), (k, int(bad.sum()), float((np.abs(a - b)[bad] / tol[bad]).max()))
 
 
 def _check_step(m, ref, n_rays, loss):
@@ -71,16 +71,16 @@ def test_c1_step_parity_fp32():
     kf = synth.c1_keyframe(0)
     m = _map(cfg, P, [kf])
     loss = m.step(4096, seed=7, no_update=True)
-    ref = oracle.forward_backward(cfg, P, [kf], 4096, 7, 0)
+    ref = oracle.forward_backward(cfg, P, [kf], 4096, 7, 0, magnitudes=True)
     _check_step(m, ref, 4096, loss)
-    _check_grads(m.unpack(m.get_grads()), ref["grads"])
+    _check_grads(m.unpack(m.get_grads()), ref)
 
 
 def test_small_multi_keyframe_occupancy_truncation_ragged():
     """Two dense and two hashed levels, a random 16^3 bitfield, at most 16 samples
     per ray (truncation), three keyframes of different sizes with z-depth, and a
     ray count that is not a multiple of any tile."""
-    cfg = synth.config_small(occ_res=16)
+    cfg = synth.config_small(occ_res=16, step=np.float32(0.02), n_steps=150)
     P = synth.random_params(cfg, 3, table_scale=0.05, mlp_std=0.2)
     rng = np.random.default_rng(4)
     kfs = []
@@ -92,10 +92,10 @@ def test_small_multi_keyframe_occupancy_truncation_ragged():
     m = _map(cfg, P, kfs, bits)
     n = 3001
     loss = m.step(n, seed=11, no_update=True)
-    ref = oracle.forward_backward(cfg, P, kfs, n, 11, 0, occ_bits=bits)
+    ref = oracle.forward_backward(cfg, P, kfs, n, 11, 0, occ_bits=bits, magnitudes=True)
     assert np.bincount(ref["ray_id"], minlength=n).max() == cfg.max_samples
     _check_step(m, ref, n, loss)
-    _check_grads(m.unpack(m.get_grads()), ref["grads"])
+    _check_grads(m.unpack(m.get_grads()), ref)
 
 
 def test_adam_update_and_step_counter():
@@ -110,8 +110,14 @@ def test_adam_update_and_step_counter():
     mm, vv = m.get_adam()
     z = {k: np.zeros_like(v, dtype=np.float64) for k, v in P.items()}
     refP, refM, refV = oracle.adam_update(P, G, z, z, 1, cfg)
+    lr = float(cfg.lr)
     for k in P:
-        assert np.allclose(newP[k], refP[k], rtol=1e-6, atol=1e-9), k
+        # the update step recomputes the gradient: entries whose terms cancel to the
+        # FP32 rounding level may change sign, and the first Adam step is +-lr there
+        firm = np.abs(G[k]) > 1e-3 * np.abs(G[k]).max()
+        # FP32 update: the lr-sized step carries ~1e-7 relative rounding
+        assert np.allclose(newP[k][firm], refP[k][firm], rtol=1e-6, atol=1e-5 * lr), k
+        assert np.all(np.abs(newP[k] - P[k]) <= lr * (1 + 1e-5)), k
     assert np.allclose(m.unpack(mm)["W4"], refM["W4"], rtol=1e-6, atol=1e-12)
     assert np.allclose(m.unpack(vv)["tables"], refV["tables"], rtol=1e-5, atol=1e-20)
     assert m.stats().step == 1
@@ -127,12 +133,13 @@ def test_adam_update_and_step_counter():
 def test_render_parity_with_early_termination():
     cfg = synth.config_small(occ_res=0, render_t_min=np.float32(1e-2))
     P = synth.random_params(cfg, 8, table_scale=0.5, mlp_std=0.3)
-    P["W2"][0] += 0.3                          # denser field: rays terminate early
+    P["W2"][0] += 1.0                          # denser field: rays terminate early
     m = _map(cfg, P, [synth.c1_keyframe(0, W=8, H=8)])
     kf = synth.c1_keyframe(9, W=48, H=36)
     rgb, D, acc = m.render(kf.c2w, kf.K, 48, 36)
     I_ref, D_ref, A_ref = oracle.render(cfg, P, kf.c2w, kf.K, 48, 36, t_min=1e-2)
-    assert np.mean(A_ref > 0.9) > 0.2
+    _, _, A_full = oracle.render(cfg, P, kf.c2w, kf.K, 48, 36)
+    assert np.mean(A_ref > 0.9) > 0.2 and np.abs(A_full - A_ref).max() > 1e-3   # termination matters
     assert np.allclose(rgb.reshape(-1, 3), I_ref, rtol=REL, atol=1e-6)
     assert np.allclose(D.ravel(), D_ref, rtol=REL, atol=1e-6)
     assert np.allclose(acc.ravel(), A_ref, rtol=REL, atol=1e-6)
@@ -153,7 +160,7 @@ def test_render_device_buffers_match_host():
 
 
 def test_occupancy_refresh_parity():
-    cfg = synth.config_small(occ_res=16)
+    cfg = synth.config_small(occ_res=16, occ_thresh=np.float32(1.5))
     P = synth.random_params(cfg, 12, table_scale=1.0, mlp_std=0.3)
     m = _map(cfg, P, [synth.c1_keyframe(0, W=8, H=8)])
     dens0 = np.random.default_rng(13).uniform(0, 0.03, 16 ** 3).astype(np.float32)
@@ -179,7 +186,8 @@ def test_edge_cases():
     with pytest.raises(MapError) as e:
         m.step(16, seed=0)
     assert e.value.code == -3                  # no keyframes
-    m.set_params(P if isinstance(P, np.ndarray) else __import__("paper_2210_13641_gb300").pack_params(P))
+    from paper_2210_13641_gb300 import pack_params
+    m.set_params(pack_params(P))
     # camera outside the box looking away: no ray has a sample
     kf = synth.c1_keyframe(3)
     kf.c2w = synth.look_at_pose([3.0, 3.0, 3.0], [6.0, 6.0, 6.0])

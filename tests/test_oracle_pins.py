@@ -454,3 +454,44 @@ def test_render_matches_training_forward_on_same_rays():
     out = oracle.forward_backward(cfg, P, [kf], kf.W * kf.H, 0, 0,
                                   rays=(np.zeros(kf.W * kf.H, int), u, v), want_grad=False)
     assert np.allclose(I, out["I_hat"], rtol=1e-14) and np.allclose(D, out["D_hat"], rtol=1e-14)
+
+
+def test_gradient_magnitudes_bound_the_gradients():
+    """grads_abs (sum of |terms|) bounds |grad| entry by entry and equals it where
+    no term changes sign (a single-sample, single-ray batch of the plain chain)."""
+    cfg, P, kf = _tiny_problem()
+    out = oracle.forward_backward(cfg, P, [kf], 64, 13, 0, magnitudes=True)
+    for k, g in out["grads"].items():
+        assert np.all(np.abs(g) <= out["grads_abs"][k] * (1 + 1e-12) + 1e-300), k
+    assert all(np.any(out["grads_abs"][k] > np.abs(out["grads"][k]) * 1.01) for k in ("W1", "W4"))
+
+
+def test_operand_rounding_and_relu_decisions():
+    """round_to: binary16 and bfloat16 round to nearest even, FP16 saturates.  ReLU
+    decisions on operands exactly representable in the MLP type equal the FP64
+    signs; on random operands a decision differs from the FP64 sign only for units
+    whose pre-activation lies within a few roundoffs of zero."""
+    r = lambda x, p: float(oracle.round_to(np.array([x]), p)[0])
+    assert r(1 + 2 ** -9, "bf16") == 1.0 and r(1 + 3 * 2 ** -9, "bf16") == 1 + 2 ** -7
+    assert r(1 + 2 ** -8, "bf16") == 1.0                   # tie to even
+    assert r(1 + 2 ** -12, "fp16") == 1.0 and r(1 + 3 * 2 ** -12, "fp16") == 1 + 2 ** -10
+    assert r(1e6, "fp16") == 65504.0
+    rng = np.random.default_rng(30)
+    shapes = {"W1": (64, 32), "W2": (16, 64), "W3": (64, 32), "W4": (64, 64), "W5": (3, 64)}
+    P = {k: rng.integers(-4, 5, s) / 8.0 for k, s in shapes.items()}
+    feat = rng.integers(-8, 9, (200, 32)) / 16.0
+    sh = rng.integers(-8, 9, (200, 16)) / 16.0
+    fw = oracle.field_forward(P, feat, sh)
+    for prec in ("fp16", "bf16"):
+        assert np.array_equal(oracle.relu_decisions(P, feat, sh, prec)[0], fw["a1"] > 0)
+    P = {k: rng.normal(0, 0.3, s) for k, s in shapes.items()}
+    feat = rng.normal(0, 0.5, (2000, 32))
+    sh = oracle.sh_deg4(rng.normal(size=(2000, 3)) / np.sqrt(3))
+    fw = oracle.field_forward(P, feat, sh)
+    A = {k: np.abs(v) for k, v in P.items()}
+    mag1 = np.abs(feat) @ A["W1"].T
+    for prec, u in (("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)):
+        m1, m3, m4 = oracle.relu_decisions(P, feat, sh, prec)
+        flip1 = m1 != (fw["a1"] > 0)
+        assert np.all(np.abs(fw["a1"][flip1]) <= 8 * u * mag1[flip1])
+        assert (m3 != (fw["a3"] > 0)).mean() < 0.05 and (m4 != (fw["a4"] > 0)).mean() < 0.05
