@@ -118,8 +118,10 @@ def test_adam_update_and_step_counter():
         # FP32 update: the lr-sized step carries ~1e-7 relative rounding
         assert np.allclose(newP[k][firm], refP[k][firm], rtol=1e-6, atol=1e-5 * lr), k
         assert np.all(np.abs(newP[k] - P[k]) <= lr * (1 + 1e-5)), k
-    assert np.allclose(m.unpack(mm)["W4"], refM["W4"], rtol=1e-6, atol=1e-12)
-    assert np.allclose(m.unpack(vv)["tables"], refV["tables"], rtol=1e-5, atol=1e-20)
+    for k, tol in (("W4", 1e-5), ("tables", 1e-5)):
+        firm = np.abs(G[k]) > 1e-3 * np.abs(G[k]).max()
+        assert np.allclose(m.unpack(mm)[k][firm], refM[k][firm], rtol=tol, atol=0), k
+        assert np.allclose(m.unpack(vv)[k][firm], refV[k][firm], rtol=2 * tol, atol=0), k
     assert m.stats().step == 1
     # the next draw uses step index 1
     m.step(1000, seed=3, no_update=True)
