@@ -32,9 +32,12 @@ sample including the last; samples outside the box or in empty cells are dropped
 (equivalently sigma = 0); background colour 0.
 
 Parity status: every function below is pinned by the not-gpu tests (closed forms,
-invariants, brute force, finite differences) except the SplitMix64 constants and
-the hash primes, which are taken from their published definitions and can only be
-checked structurally ("parity unpinned" for those constants).
+invariants, brute force, finite differences, the published SplitMix64 output
+sequence).  One constant set is "parity unpinned": the three spatial-hash primes of
+vertex_index are taken from the cited Instant-NGP paper (the NeRF-SLAM paper does
+not restate them); the tests pin the hash's structure (first prime 1, uint32
+wrap-around, xor of the axis terms, uniform bucket fill) but nothing outside this
+file fixes the primes' digits.
 """
 
 from __future__ import annotations
