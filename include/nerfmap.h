@@ -240,6 +240,41 @@ int map_get_stats(map_handle h, map_stats* out);
 int map_profile_enable(map_handle h, int enable);
 int map_profile_read(map_handle h, double* ms, uint64_t* count, uint64_t* launches);
 
+/*
+ * map_march_noalloc - the march and sample compaction of a mapping step (sample
+ * positions, box and occupancy tests, first max_samples kept per ray, compacted in
+ * ray order) for callers that cannot allocate device memory.  The paper has no
+ * counterpart: it is a deployment variant of the library's march kernel.
+ *
+ * Who needs it: a caller whose GPU memory belongs to another allocator (a
+ * framework's caching allocator that has reserved the device, or a fixed memory
+ * budget), or a latency-critical host loop for which a cudaMalloc, which may
+ * synchronise the device, would stall.  map_step and map_render allocate their
+ * work buffers in the map; this call allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.  Its only scratch (per-ray counts and
+ * scan totals) is a static device array of about 4 MB that every GPU loading the
+ * library holds until the process exits.
+ *
+ * cfg: the march fields are used (near_t, step_t, n_steps, max_samples,
+ *   grid_origin, grid_inv_size, box_max, occ_res).  occ_bits: device bitfield
+ *   (layout as map_set_occupancy), required when occ_res > 0, ignored otherwise.
+ * rays_o, rays_d: device arrays [n_rays][3] (origin, unit direction).
+ * n_rays: 1 .. 1048576 (the scratch size); larger values fail with MAP_EINVAL.
+ * offsets: device [n_rays + 1], receives the exclusive scan of the per-ray sample
+ *   counts (offsets[n_rays] = total); ray_id, t: device [cap_samples], receive
+ *   the samples in ray order; cap_samples >= n_rays * max_samples is required.
+ * stream: all work is queued on it; the call returns without waiting.
+ * The first call on a device looks up the scratch array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  All calls share the scratch array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the caller.
+ * Errors: MAP_EINVAL (argument), MAP_ECUDA (address lookup or launch); the message
+ * is available from map_last_error(NULL) until this thread's next successful call.
+ */
+int map_march_noalloc(const map_config* cfg, const uint8_t* occ_bits, const float* rays_o,
+                      const float* rays_d, uint32_t n_rays, uint32_t* offsets, uint32_t* ray_id,
+                      float* t, size_t cap_samples, void* stream);
+
 /* sizeof(map_config) as compiled into the library, so a binding can check that its
  * own copy of the struct has the same layout. */
 size_t map_abi_config_size(void);

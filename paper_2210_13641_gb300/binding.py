@@ -87,6 +87,9 @@ _SIGS = {
                                            ctypes.c_size_t, ctypes.c_void_p]),
     "map_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MapStats)]),
     "map_abi_config_size": (ctypes.c_size_t, []),
+    "map_march_noalloc": (ctypes.c_int, [ctypes.POINTER(MapConfig), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "map_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "map_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "map_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),

@@ -12,6 +12,8 @@
 
 using namespace nm;
 
+const char* nm_noalloc_last_error();
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -673,6 +675,10 @@ int map_profile_read(map_handle h, double* ms, uint64_t* count, uint64_t* launch
 
 size_t map_abi_config_size(void) { return sizeof(map_config); }
 
-const char* map_last_error(map_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+const char* map_last_error(map_handle h) {
+    if (h) return h->err.c_str();
+    const char* m = nm_noalloc_last_error();
+    return m[0] ? m : g_create_error.c_str();
+}
 
 }  // extern "C"

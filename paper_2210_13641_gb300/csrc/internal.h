@@ -49,6 +49,9 @@ void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t 
 void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, const StepBufs& b,
                   cudaStream_t s);
 
+void launch_scan_counts(const uint32_t* counts, uint32_t n, uint32_t* offsets, uint32_t* tile_sums,
+                        cudaStream_t s);
+
 // k_field_fp32.cu
 void launch_field_fwd_fp32(const DevCfg& c, const float* params, uint32_t n_rays,
                            const StepBufs& b, bool store_feat, int n_sm, cudaStream_t s);

@@ -237,3 +237,17 @@ void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, co
 }
 
 }  // namespace nm
+
+namespace nm {
+
+// Exclusive scan of counts[0..n) into offsets[0..n] with caller-provided tile-sum
+// storage of at least ceil(n / 4096) entries (used by the allocation-free march).
+void launch_scan_counts(const uint32_t* counts, uint32_t n, uint32_t* offsets, uint32_t* tile_sums,
+                        cudaStream_t s) {
+    const uint32_t n_tiles = (n + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<n_tiles, kScanThreads, 0, s>>>(counts, n, offsets, tile_sums);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(tile_sums, n_tiles, offsets + n);
+    k_scan_add<<<(n + 255) / 256, 256, 0, s>>>(offsets, n, tile_sums);
+}
+
+}  // namespace nm
