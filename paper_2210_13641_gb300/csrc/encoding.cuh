@@ -77,6 +77,63 @@ __device__ __forceinline__ void hash_scatter(const DevCfg& c, float2* __restrict
     }
 }
 
+// Warp-cooperative form of hash_scatter, called by all 32 lanes (lanes with
+// valid = false contribute nothing).  Consecutive samples of a ray fall into the
+// same cell of the coarse levels, so per level the lanes with equal cells (runs of
+// consecutive lanes) first sum their 8 corner contributions with a segmented
+// shuffle reduction, and only the first lane of each run issues the 8 atomics.
+// A level whose 32 cells are all different skips the reduction.
+__device__ __forceinline__ void hash_scatter_warp(const DevCfg& c, float2* __restrict__ gtables,
+                                                  float3 x, const float* df, bool valid) {
+    const uint32_t Tmask = c.T - 1;
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int l = 0; l < kEnc / 2; ++l) {
+        if (l >= (int)c.L) break;
+        const uint32_t N = c.res[l];
+        const bool dense = (c.dense_mask >> l) & 1u;
+        uint32_t cx, cy, cz;
+        float wx, wy, wz;
+        level_cell(x.x, N, cx, wx);
+        level_cell(x.y, N, cy, wy);
+        level_cell(x.z, N, cz, wz);
+        float2* gtab = gtables + (size_t)l * c.T;
+        const float g0 = valid ? df[2 * l] : 0.f, g1 = valid ? df[2 * l + 1] : 0.f;
+        const uint64_t key = valid ? (((uint64_t)cz << 42) | ((uint64_t)cy << 21) | cx) : ~(uint64_t)lane;
+        const uint64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool head = lane == 0 || prev != key;
+        const uint32_t heads = __ballot_sync(0xffffffffu, head);
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float wk = corner_weight(k, wx, wy, wz);
+            v[2 * k] = wk * g0;
+            v[2 * k + 1] = wk * g1;
+        }
+        if (heads != 0xffffffffu) {
+            // lanes lane .. run_end form this lane's run; the head ends up with the sum
+            const uint32_t above = (lane == 31u) ? 0u : (heads & ~((2u << lane) - 1u));
+            const uint32_t run_end = above ? (uint32_t)(__ffs(above) - 2) : 31u;
+            const uint32_t max_len = __reduce_max_sync(0xffffffffu, head ? run_end - lane + 1u : 1u);
+            for (uint32_t off = 1; off < max_len; off <<= 1) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float o = __shfl_down_sync(0xffffffffu, v[q], off);
+                    if (lane + off <= run_end) v[q] += o;
+                }
+            }
+        }
+        if (head && valid) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t slot = vertex_slot(cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1), N,
+                                                  dense, Tmask);
+                atomicAdd(gtab + slot, make_float2(v[2 * k], v[2 * k + 1]));
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
 
 }  // namespace nm

@@ -337,18 +337,20 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
         }
         __syncthreads();
         tile_outer(s.act, kRh1, kRf, kHid, kEnc, s.dW + kOffW1);    // dW1 = dA1^T f
-        // df = W1^T dA1, scattered into the tables
-        if (valid) {
+        // df = W1^T dA1, scattered into the tables (all lanes take part)
+        {
             float df[kEnc];
 #pragma unroll
             for (int k = 0; k < kEnc; ++k) df[k] = 0.f;
+            if (valid) {
 #pragma unroll 2
-            for (int j = 0; j < kHid; ++j) {
-                const float a = row[kRh1 + j];
+                for (int j = 0; j < kHid; ++j) {
+                    const float a = row[kRh1 + j];
 #pragma unroll
-                for (int k = 0; k < kEnc; ++k) df[k] += W1[j * kEnc + k] * a;
+                    for (int k = 0; k < kEnc; ++k) df[k] += W1[j * kEnc + k] * a;
+                }
             }
-            hash_scatter(c, gtables, x, df);
+            hash_scatter_warp(c, gtables, x, df, valid);
         }
         __syncthreads();
     }

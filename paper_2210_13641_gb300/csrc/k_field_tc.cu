@@ -491,11 +491,9 @@ __global__ void __launch_bounds__(128) k_field_bwd_tc(DevCfg c, const float* __r
         }
         wait_mma(&bar, phase, timed_out);
         ld_cols<32>(trow, 0, v);
-        if (valid && !timed_out) {
 #pragma unroll
-            for (int k = 0; k < kEnc; ++k) v[k] *= inv_S;
-            hash_scatter(c, gtables, x, v);
-        }
+        for (int k = 0; k < kEnc; ++k) v[k] *= inv_S;
+        hash_scatter_warp(c, gtables, x, v, valid && !timed_out);
         first = false;
         fence_before_sync();
         if (__syncthreads_or(timed_out)) {
