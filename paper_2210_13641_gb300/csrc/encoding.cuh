@@ -14,38 +14,52 @@ __device__ __forceinline__ float corner_weight(int k, float wx, float wy, float 
 }
 
 // Encodes grid position x into f[0 .. 2L) (f[2L .. 32) set to zero).
-// tables: [L][T] float2.
+// tables: [L][T] float2.  Levels are processed in groups of kGatherGroup: the
+// group's 8 * kGatherGroup slots are computed first and all its loads issued
+// before any is used, so that many table reads are in flight per thread.
+constexpr int kGatherGroup = 4;
+
 __device__ __forceinline__ void hash_encode(const DevCfg& c, const float2* __restrict__ tables,
                                             float3 x, float* f) {
     const uint32_t Tmask = c.T - 1;
 #pragma unroll
-    for (int l = 0; l < kEnc / 2; ++l) {
-        float a0 = 0.f, a1 = 0.f;
-        if (l < (int)c.L) {
-            const uint32_t N = c.res[l];
-            const bool dense = (c.dense_mask >> l) & 1u;
-            uint32_t cx, cy, cz;
-            float wx, wy, wz;
-            level_cell(x.x, N, cx, wx);
-            level_cell(x.y, N, cy, wy);
-            level_cell(x.z, N, cz, wz);
-            const float2* tab = tables + (size_t)l * c.T;
-            float2 v[8];
+    for (int l0 = 0; l0 < kEnc / 2; l0 += kGatherGroup) {
+        float2 v[kGatherGroup][8];
+        float w[kGatherGroup][3];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t slot = vertex_slot(cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1),
-                                                  N, dense, Tmask);
-                v[k] = __ldg(tab + slot);
-            }
+        for (int g = 0; g < kGatherGroup; ++g) {
+            const int l = l0 + g;
+            if (l < (int)c.L) {
+                const uint32_t N = c.res[l];
+                const bool dense = (c.dense_mask >> l) & 1u;
+                uint32_t cx, cy, cz;
+                level_cell(x.x, N, cx, w[g][0]);
+                level_cell(x.y, N, cy, w[g][1]);
+                level_cell(x.z, N, cz, w[g][2]);
+                const float2* tab = tables + (size_t)l * c.T;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const float wk = corner_weight(k, wx, wy, wz);
-                a0 += wk * v[k].x;
-                a1 += wk * v[k].y;
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t slot = vertex_slot(cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1),
+                                                      N, dense, Tmask);
+                    v[g][k] = __ldg(tab + slot);
+                }
             }
         }
-        f[2 * l] = a0;
-        f[2 * l + 1] = a1;
+#pragma unroll
+        for (int g = 0; g < kGatherGroup; ++g) {
+            const int l = l0 + g;
+            float a0 = 0.f, a1 = 0.f;
+            if (l < (int)c.L) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float wk = corner_weight(k, w[g][0], w[g][1], w[g][2]);
+                    a0 += wk * v[g][k].x;
+                    a1 += wk * v[g][k].y;
+                }
+            }
+            f[2 * l] = a0;
+            f[2 * l + 1] = a1;
+        }
     }
 }
 
