@@ -41,7 +41,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    p.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"])
+    p.add_argument("--no-forms", action="store_true", help="skip timing the other MLP precisions")
     p.add_argument("--rays", type=int, default=N_RAYS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
@@ -269,6 +270,21 @@ def main():
             "frac": achieved / hbm, "traffic": None,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "phase_ms_per_step": {k: v["ms"] / max(v["count"], 1) for k, v in prof.items() if v["count"]}}
+    # the tables are L2-resident: also compare the table traffic with the measured
+    # random-access ceiling for a table of this size (uniform 8-byte reads / reductions)
+    from paper_2210_13641_gb300 import binding as _b
+    tab = torch.zeros((cfg.n_levels << cfg.log2_table, 2), device="cuda")
+    g = _b.probe_random_access(tab, per_thread=64, mode=0)
+    a = _b.probe_random_access(tab, per_thread=64, mode=1)
+    del tab
+    table_bytes = n_samples * 8 * cfg.n_levels * cfg.n_features * 4
+    fwd_gbs = table_bytes / (cand["field_fwd"] / 1e3) / 1e9
+    bwd_gbs = table_bytes / (cand["field_bwd"] / 1e3) / 1e9
+    roof["random_access_ceiling"] = {
+        "table_mb": (cfg.n_levels << cfg.log2_table) * 8 / 2 ** 20,
+        "gather_gbs": g["payload_gbs"], "atomic_gbs": a["payload_gbs"],
+        "field_fwd_table_gbs": fwd_gbs, "field_fwd_frac_of_gather": fwd_gbs / g["payload_gbs"],
+        "field_bwd_table_gbs": bwd_gbs, "field_bwd_frac_of_atomic": bwd_gbs / a["payload_gbs"]}
 
     # ---------------- end to end: keyframe upload from pinned host memory + step + loss read
     pinned = []
@@ -313,6 +329,39 @@ def main():
     torch.cuda.synchronize()
     render_mpx = W * H * nv / (r0.elapsed_time(r1) / 1e3) / 1e6 * world
 
+    # ---------------- the other MLP precisions on the same workload (FP32 plain form, BF16)
+    m.close()
+    forms = {args.precision: {"value": value, "ms_per_step": ms / args.steps}}
+    if not args.no_forms:
+        for prec in ("fp32", "fp16", "bf16"):
+            if prec == args.precision:
+                continue
+            mf = NerfMap(cfg.replace(precision=prec), occ_every=0)
+            mf.set_params(pack_params(params))
+            mf.set_occupancy(bits)
+            for kf in kfs:
+                mf.add_keyframe(kf)
+            for i in range(2):
+                mf.step(n, seed=1000 + i, want_loss=False, stream=stream)
+            k = max(3, min(args.steps, 6))
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for i in range(k):
+                mf.step(n, seed=2000 + i, want_loss=False, stream=stream)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            fms = f0.elapsed_time(f1)
+            if dist:
+                t = torch.tensor([fms], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                fms = float(t.item())
+            forms[prec] = {"value": n * k * world / (fms / 1e3), "ms_per_step": fms / k}
+            mf.close()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -324,11 +373,10 @@ def main():
                            "l2": "working set > L2: params+grads+Adam moments (0.27 GB) streamed every step",
                            "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
                 "roofline": roof, "render_mpx_s": render_mpx, "e2e": e2e, "clocks": clk,
-                "gpu_launches": int(launches)}
+                "gpu_launches": int(launches), "forms": forms}
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
-    m.close()
     if dist:
         dist.destroy_process_group()
 

@@ -275,6 +275,17 @@ int map_march_noalloc(const map_config* cfg, const uint8_t* occ_bits, const floa
                       const float* rays_d, uint32_t n_rays, uint32_t* offsets, uint32_t* ray_id,
                       float* t, size_t cap_samples, void* stream);
 
+/*
+ * map_probe_random_access - measurement kernel (no counterpart in the paper): the
+ * ceiling for the hash-grid traffic.  n_threads threads each make per_thread
+ * accesses to uniformly random entries of `table` (device, n_entries float2 pairs,
+ * n_entries a power of two): mode 0 reads them (8 bytes each), mode 1 adds
+ * (1e-30, 1e-30) to them with FP32 vector reductions.  sink: device, 2 floats.
+ * Queued on `stream`; the caller times it.  Returns MAP_EINVAL on bad arguments.
+ */
+int map_probe_random_access(float* table, uint64_t n_entries, uint32_t n_threads, uint32_t per_thread,
+                            int mode, uint64_t seed, float* sink, void* stream);
+
 /* sizeof(map_config) as compiled into the library, so a binding can check that its
  * own copy of the struct has the same layout. */
 size_t map_abi_config_size(void);
