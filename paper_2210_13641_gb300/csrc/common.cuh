@@ -101,6 +101,40 @@ __device__ __forceinline__ bool occupied(const DevCfg& c, const uint32_t* __rest
     return (__ldg(bits + (b >> 5)) >> (b & 31)) & 1u;
 }
 
+// Step range [i_lo, i_hi) outside which no step of the ray can pass the box test.
+// The slab interval [t_in, t_out] of the ray in grid coordinates is computed in
+// FP32 and widened by two steps plus a relative 1e-5: the positions of the steps
+// are rounded by about 1e-7 of their magnitude, far inside that margin, so every
+// step whose FP32 position is in the box lies in the range (the box test itself
+// is still taken per step).
+__device__ __forceinline__ void box_step_range(const DevCfg& c, float3 o, float3 d, uint32_t& i_lo,
+                                               uint32_t& i_hi) {
+    const float xo[3] = {(o.x - c.org[0]) * c.inv_size, (o.y - c.org[1]) * c.inv_size,
+                         (o.z - c.org[2]) * c.inv_size};
+    const float xd[3] = {d.x * c.inv_size, d.y * c.inv_size, d.z * c.inv_size};
+    float t_in = -3.0e38f, t_out = 3.0e38f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (fabsf(xd[a]) > 1e-20f) {
+            const float t0 = (0.f - xo[a]) / xd[a], t1 = (c.box[a] - xo[a]) / xd[a];
+            t_in = fmaxf(t_in, fminf(t0, t1));
+            t_out = fminf(t_out, fmaxf(t0, t1));
+        } else if (!(xo[a] >= -1e-6f && xo[a] <= c.box[a] + 1e-6f)) {
+            t_out = -3.0e38f;  // parallel to this slab and outside it
+        }
+    }
+    const float margin_lo = 2.f * c.step_t + 1e-5f * fabsf(t_in);
+    const float margin_hi = 2.f * c.step_t + 1e-5f * fabsf(t_out);
+    const float lo = (t_in - margin_lo - c.near_t) / c.step_t;
+    const float hi = (t_out + margin_hi - c.near_t) / c.step_t;
+    if (!(hi >= lo) || hi < 0.f) {  // misses the box even with the margins
+        i_lo = i_hi = 0;
+        return;
+    }
+    i_lo = lo <= 0.f ? 0u : (lo >= (float)c.n_steps ? c.n_steps : (uint32_t)lo);
+    i_hi = hi >= (float)c.n_steps ? c.n_steps : (uint32_t)hi + 1u;
+}
+
 // ----------------------------------------------------------------- hash grid
 
 // Table slot of vertex (cx, cy, cz) at resolution N of a level (dense or hashed).

@@ -297,6 +297,7 @@ __global__ void __launch_bounds__(128) k_field_bwd_tc(DevCfg c, const float* __r
                                                       uint32_t cap, const uint32_t* __restrict__ n_total,
                                                       const uint32_t* __restrict__ ray_id,
                                                       const float* __restrict__ ts, const uint4* __restrict__ feat,
+                                                      const float4* __restrict__ sig_rgb,
                                                       const float4* __restrict__ dsig_rgb, float feat_scale,
                                                       const float* __restrict__ seed_max, uint32_t* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -342,10 +343,11 @@ __global__ void __launch_bounds__(128) k_field_bwd_tc(DevCfg c, const float* __r
         const bool valid = i < n;
         float v[64];
         float3 x = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 0.f);
-        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f), col = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid) {
             x = sample_pos_tc(c, rays, cap, ray_id[i], ts[i], d);
             g = dsig_rgb[i];
+            col = sig_rgb[i];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 *reinterpret_cast<uint4*>(tX0 + tile_offset(tid, 8 * q, 128)) = feat[(size_t)i * 4 + q];
@@ -419,15 +421,9 @@ __global__ void __launch_bounds__(128) k_field_bwd_tc(DevCfg c, const float* __r
             v[k] = fmaxf(v[k], 0.f);
         }
         store_row<BF16, 64>(tH4, tid, v);
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tH4, 128), kmaj(sW5, 16), 4, kM128N16, false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<16>(trow, 0, v);
         {
-            const float c0 = sigmoidf_(v[0]), c1 = sigmoidf_(v[1]), c2 = sigmoidf_(v[2]);
+            // the colours need no layer-5 recompute: the forward kernel stored them
+            const float c0 = col.y, c1 = col.z, c2 = col.w;
             v[0] = S * g.y * c0 * (1.f - c0);
             v[1] = S * g.z * c1 * (1.f - c1);
             v[2] = S * g.w * c2 * (1.f - c2);
@@ -562,7 +558,7 @@ static void bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t 
     const float fs = BF16 ? 1.f : 256.f;
     k_field_bwd_tc<BF16><<<n_sm * 2, 128, kBwdSmem, s>>>(c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays,
                                                           b.ray_id, b.t, reinterpret_cast<const uint4*>(b.feat),
-                                                          b.dsig_rgb, fs, b.loss, b.err);
+                                                          b.sig_rgb, b.dsig_rgb, fs, b.loss, b.err);
 }
 
 void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b, bool store_feat,

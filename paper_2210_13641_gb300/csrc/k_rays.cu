@@ -126,7 +126,9 @@ __global__ void k_march(DevCfg c, const uint32_t* __restrict__ bits, uint32_t n_
     const float3 d = make_float3(rays[kDx * cap + r], rays[kDy * cap + r], rays[kDz * cap + r]);
     uint32_t n = 0;
     const uint32_t base = kEmit ? offsets[r] : 0;
-    for (uint32_t i = 0; i < c.n_steps && n < c.max_samples; ++i) {
+    uint32_t i_lo, i_hi;
+    box_step_range(c, o, d, i_lo, i_hi);
+    for (uint32_t i = i_lo; i < i_hi && n < c.max_samples; ++i) {
         const float t = sample_t(c, i);
         const float3 x = grid_pos(c, o, d, t);
         if (!in_box(c, x) || !occupied(c, bits, x)) continue;
