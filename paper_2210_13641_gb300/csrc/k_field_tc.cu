@@ -155,7 +155,6 @@ constexpr int kT32 = 128 * 32 * 2, kT64 = 128 * 64 * 2, kT16 = 128 * 16 * 2;
 }  // namespace
 
 constexpr int kFwdSmem = kWB + kT32 + kT64 + kT64;                     // 61440
-constexpr int kBwdSmem = kWB + kT32 + kT64 + kT32 + kT64 + kT64 + kT16;  // 90112
 
 // ------------------------------------------------------------------ forward
 template <bool BF16>
@@ -286,20 +285,107 @@ __global__ void __launch_bounds__(128) k_field_fwd_tc(DevCfg c, const float* __r
 }
 
 // ------------------------------------------------------------------ backward
+// Warp-specialised: warps 0-3 (the "MLP" group, thread r = sample row r = TMEM
+// lane r) run the layer chain on the tensor cores; warps 4-7 (the "IO" group,
+// thread 128 + r serves row r) load each tile's inputs one tile ahead and scatter
+// each finished tile's encoding gradient into the tables while the MLP group
+// works on the next tile.  The groups hand tiles over through named barriers:
+//   kBarIn      IO -> MLP  the tile's encodings (X0) and row data are in place
+//   kBarDfReady MLP -> IO  the chain is done (X0 free) and dL/dfeat is in smem
+//   kBarDfFree  IO -> MLP  the dL/dfeat buffer has been read
+// Both groups walk the same tile list and meet every barrier, whatever happens
+// to an MMA wait (a timed-out wait only skips waiting), so no barrier can block.
+//
 // TMEM columns: [0,64) layer chain, [64,128) dW4, [128,160) dW3, [160,192) dW1,
 // [192,208) dW2^T, [208,224) dW5^T.  The weight gradients are M=64 products: row m
 // of such an accumulator is TMEM lane 32*(m/16) + m%16.
 constexpr uint32_t kColW4 = 64, kColW3 = 128, kColW1 = 160, kColW2T = 192, kColW5T = 208;
+constexpr int kBarMlp = 1, kBarIn = 2, kBarDfReady = 3, kBarDfFree = 4;
+constexpr int kDfBytes = 128 * 32 * 4;      // dL/dfeat rows, 16-byte chunks xor-swizzled by row
+constexpr int kRowBytes = 128 * 32;         // row data: {d.xyz, valid}, {dz0, dz1, dz2, dL/dsigma}
+constexpr int kBwdSmem = kWB + kT32 + kT64 + kT32 + kT64 + kT64 + kT16 + kDfBytes + kRowBytes;  // 110592
+
+namespace {
+
+__device__ __forceinline__ void nb_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void nb_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+
+// to_tensor() for the 128 threads of the MLP group only.
+__device__ __forceinline__ void to_tensor_mlp() {
+    fence_proxy_async();
+    fence_before_sync();
+    nb_sync(kBarMlp, 128);
+    fence_after_sync();
+}
+
+// C columns of row r of a 128-row tile from C floats, starting at column c0.
+template <bool BF16, int C>
+__device__ __forceinline__ void store_row_at(uint8_t* tile, int r, int c0, const float* v) {
+#pragma unroll
+    for (int g = 0; g < C / 8; ++g) {
+        uint4 q;
+        q.x = pack2<BF16>(v[8 * g + 0], v[8 * g + 1]);
+        q.y = pack2<BF16>(v[8 * g + 2], v[8 * g + 3]);
+        q.z = pack2<BF16>(v[8 * g + 4], v[8 * g + 5]);
+        q.w = pack2<BF16>(v[8 * g + 6], v[8 * g + 7]);
+        *reinterpret_cast<uint4*>(tile + tile_offset(r, c0 + 8 * g, 128)) = q;
+    }
+}
+
+// 64 accumulator columns -> relu(scale * a) into a 64-column tile; the ReLU branch
+// of each column is returned as two 32-bit masks.
+template <bool BF16>
+__device__ __forceinline__ void relu_epilogue(uint32_t trow, uint8_t* tile, int r, float scale, uint32_t& ma,
+                                              uint32_t& mb) {
+    float v[32];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        ld_cols<32>(trow, 32 * h, v);
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const float a = v[k] * scale;
+            if (a > 0.f) m |= 1u << k;
+            v[k] = fmaxf(a, 0.f);
+        }
+        store_row_at<BF16, 32>(tile, r, 32 * h, v);
+        if (h == 0) ma = m;
+        else mb = m;
+    }
+}
+
+// 64 accumulator columns masked by the ReLU branches into a 64-column tile.
+template <bool BF16>
+__device__ __forceinline__ void mask_epilogue(uint32_t trow, uint8_t* tile, int r, uint32_t ma, uint32_t mb) {
+    float v[32];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        ld_cols<32>(trow, 32 * h, v);
+        const uint32_t m = h == 0 ? ma : mb;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = ((m >> k) & 1u) ? v[k] : 0.f;
+        store_row_at<BF16, 32>(tile, r, 32 * h, v);
+    }
+}
+
+__device__ __forceinline__ uint32_t df_offset(int r, int q) { return (uint32_t)(r * 128 + ((q ^ (r & 7)) << 4)); }
+
+}  // namespace
 
 template <bool BF16>
-__global__ void __launch_bounds__(128) k_field_bwd_tc(DevCfg c, const float* __restrict__ params,
-                                                      float* __restrict__ grads, const float* __restrict__ rays,
-                                                      uint32_t cap, const uint32_t* __restrict__ n_total,
-                                                      const uint32_t* __restrict__ ray_id,
-                                                      const float* __restrict__ ts, const uint4* __restrict__ feat,
-                                                      const float4* __restrict__ sig_rgb,
-                                                      const float4* __restrict__ dsig_rgb, float feat_scale,
-                                                      const float* __restrict__ seed_max, uint32_t* __restrict__ err) {
+__global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* __restrict__ params,
+                                                         float* __restrict__ grads, const float* __restrict__ rays,
+                                                         uint32_t cap, const uint32_t* __restrict__ n_total,
+                                                         const uint32_t* __restrict__ ray_id,
+                                                         const float* __restrict__ ts, const uint4* __restrict__ feat,
+                                                         const float4* __restrict__ sig_rgb,
+                                                         const float4* __restrict__ dsig_rgb, float feat_scale,
+                                                         const float* __restrict__ seed_max,
+                                                         uint32_t* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tslot;
@@ -308,14 +394,16 @@ __global__ void __launch_bounds__(128) k_field_bwd_tc(DevCfg c, const float* __r
     uint8_t* sW3 = sW2 + kW2B;
     uint8_t* sW4 = sW3 + kW3B;
     uint8_t* sW5 = sW4 + kW4B;
-    uint8_t* tX0 = smem + kWB;   // 128 x 32
+    uint8_t* tX0 = smem + kWB;   // 128 x 32, written by the IO group
     uint8_t* tH1 = tX0 + kT32;   // 128 x 64  (later G1)
     uint8_t* tX3 = tH1 + kT64;   // 128 x 32  (later G2 in columns 0..15)
     uint8_t* tH3 = tX3 + kT32;   // 128 x 64  (later G3)
     uint8_t* tH4 = tH3 + kT64;   // 128 x 64  (later G4)
     uint8_t* tG5 = tH4 + kT64;   // 128 x 16
+    uint8_t* sDf = tG5 + kT16;   // 128 rows x 32 FP32
+    float4* sRow = reinterpret_cast<float4*>(sDf + kDfBytes);  // [128][2]
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, r = tid & 127;
     load_weight_tiles<BF16>(params + (size_t)c.L * c.T * 2, sW1, sW2, sW3, sW4, sW5);
     if (warp == 0) tmem_alloc(&tslot, 256);
     if (tid == 0) {
@@ -324,205 +412,217 @@ __global__ void __launch_bounds__(128) k_field_bwd_tc(DevCfg c, const float* __r
     }
     to_tensor();
     const uint32_t tmem = tslot;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     const uint32_t n = *n_total;
     const uint32_t n_tiles = (n + 127) / 128;
-    float2* gtables = reinterpret_cast<float2*>(grads);
-    const float inv_fs = 1.f / feat_scale;
+    const uint32_t n_mine = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const float gm = seed_max[1];
     const float S = gm > 0.f ? exp2f(fminf(fmaxf(floorf(log2f(8192.f / gm)), -100.f), 100.f)) : 1.f;
     const float inv_S = 1.f / S;
-    uint32_t phase = 0;
     bool timed_out = false;
-    bool first = true;
-    constexpr uint32_t kM128N64 = idesc_f16(128, 64, BF16, false, false);
-    constexpr uint32_t kM128N16 = idesc_f16(128, 16, BF16, false, false);
 
-    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint32_t i = tile * 128 + tid;
-        const bool valid = i < n;
-        float v[64];
-        float3 x = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 0.f);
-        float4 g = make_float4(0.f, 0.f, 0.f, 0.f), col = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid) {
-            x = sample_pos_tc(c, rays, cap, ray_id[i], ts[i], d);
-            g = dsig_rgb[i];
-            col = sig_rgb[i];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<uint4*>(tX0 + tile_offset(tid, 8 * q, 128)) = feat[(size_t)i * 4 + q];
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<uint4*>(tX0 + tile_offset(tid, 8 * q, 128)) = make_uint4(0u, 0u, 0u, 0u);
-        }
-        // ---- forward recompute (same arithmetic as the forward kernel)
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tX0, 128), kmaj(sW1, 64), 2, kM128N64, false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<64>(trow, 0, v);
-        uint32_t m1a = 0, m1b = 0, m3a = 0, m3b = 0, m4a = 0, m4b = 0;
-#pragma unroll
-        for (int k = 0; k < 64; ++k) {
-            const float a = v[k] * inv_fs;
-            if (a > 0.f) {
-                if (k < 32) m1a |= 1u << k;
-                else m1b |= 1u << (k - 32);
+    if (warp < 4) {
+        // ======================= MLP group: the layer chain on the tensor cores
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        const float inv_fs = 1.f / feat_scale;
+        uint32_t phase = 0;
+        constexpr uint32_t kM128N64 = idesc_f16(128, 64, BF16, false, false);
+        constexpr uint32_t kM128N16 = idesc_f16(128, 16, BF16, false, false);
+        for (uint32_t k = 0; k < n_mine; ++k) {
+            nb_sync(kBarIn, 256);
+            const float4 rd = sRow[2 * r], rz = sRow[2 * r + 1];
+            const bool valid = rd.w != 0.f;
+            float v[32];
+            uint32_t m1a, m1b, m3a, m3b, m4a, m4b;
+            // ---- forward recompute (same arithmetic as the forward kernel)
+            to_tensor_mlp();
+            if (r == 0) {
+                gemm(tmem, kmaj(tX0, 128), kmaj(sW1, 64), 2, kM128N64, false);
+                mma_commit(&bar);
             }
-            v[k] = fmaxf(a, 0.f);
-        }
-        store_row<BF16, 64>(tH1, tid, v);
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tH1, 128), kmaj(sW2, 16), 4, kM128N16, false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<16>(trow, 0, v);
-        const float sigma = expf(v[0]);
-        if (valid) sh16(d.x, d.y, d.z, v + kGeo);
-        else {
-#pragma unroll
-            for (int k = kGeo; k < 32; ++k) v[k] = 0.f;
-        }
-        store_row<BF16, 32>(tX3, tid, v);
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tX3, 128), kmaj(sW3, 64), 2, kM128N64, false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<64>(trow, 0, v);
-#pragma unroll
-        for (int k = 0; k < 64; ++k) {
-            if (v[k] > 0.f) {
-                if (k < 32) m3a |= 1u << k;
-                else m3b |= 1u << (k - 32);
+            wait_mma(&bar, phase, timed_out);
+            relu_epilogue<BF16>(trow, tH1, r, inv_fs, m1a, m1b);
+            to_tensor_mlp();
+            if (r == 0) {
+                gemm(tmem, kmaj(tH1, 128), kmaj(sW2, 16), 4, kM128N16, false);
+                mma_commit(&bar);
             }
-            v[k] = fmaxf(v[k], 0.f);
-        }
-        store_row<BF16, 64>(tH3, tid, v);
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tH3, 128), kmaj(sW4, 64), 4, kM128N64, false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<64>(trow, 0, v);
+            wait_mma(&bar, phase, timed_out);
+            float y[32];
+            ld_cols<16>(trow, 0, y);
+            const float sigma = expf(y[0]);
+            if (valid) sh16(rd.x, rd.y, rd.z, y + kGeo);
+            else {
 #pragma unroll
-        for (int k = 0; k < 64; ++k) {
-            if (v[k] > 0.f) {
-                if (k < 32) m4a |= 1u << k;
-                else m4b |= 1u << (k - 32);
+                for (int q = kGeo; q < 32; ++q) y[q] = 0.f;
             }
-            v[k] = fmaxf(v[k], 0.f);
-        }
-        store_row<BF16, 64>(tH4, tid, v);
-        {
-            // the colours need no layer-5 recompute: the forward kernel stored them
-            const float c0 = col.y, c1 = col.z, c2 = col.w;
-            v[0] = S * g.y * c0 * (1.f - c0);
-            v[1] = S * g.z * c1 * (1.f - c1);
-            v[2] = S * g.w * c2 * (1.f - c2);
+            store_row_at<BF16, 32>(tX3, r, 0, y);
+            to_tensor_mlp();
+            if (r == 0) {
+                gemm(tmem, kmaj(tX3, 128), kmaj(sW3, 64), 2, kM128N64, false);
+                mma_commit(&bar);
+            }
+            wait_mma(&bar, phase, timed_out);
+            relu_epilogue<BF16>(trow, tH3, r, 1.f, m3a, m3b);
+            to_tensor_mlp();
+            if (r == 0) {
+                gemm(tmem, kmaj(tH3, 128), kmaj(sW4, 64), 4, kM128N64, false);
+                mma_commit(&bar);
+            }
+            wait_mma(&bar, phase, timed_out);
+            relu_epilogue<BF16>(trow, tH4, r, 1.f, m4a, m4b);
+            // the colours' gradient seed dz (FP32, scaled by S) comes from the IO group
+            v[0] = rz.x;
+            v[1] = rz.y;
+            v[2] = rz.z;
 #pragma unroll
-            for (int k = 3; k < 16; ++k) v[k] = 0.f;
-        }
-        store_row<BF16, 16>(tG5, tid, v);
-        // ---- backward: dW5^T += H4^T G5 ; dH4 = G5 W5
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem + kColW5T, mnmaj(tH4, 128), mnmaj(tG5, 128), 8, idesc_f16(64, 16, BF16, true, true), !first);
-            gemm(tmem, kmaj(tG5, 128), mnmaj(sW5, 16), 1, idesc_f16(128, 64, BF16, false, true), false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<64>(trow, 0, v);
+            for (int q = 3; q < 16; ++q) v[q] = 0.f;
+            store_row_at<BF16, 16>(tG5, r, 0, v);
+            // ---- backward: dW5^T += H4^T G5 ; dH4 = G5 W5
+            to_tensor_mlp();
+            if (r == 0) {
+                gemm(tmem + kColW5T, mnmaj(tH4, 128), mnmaj(tG5, 128), 8, idesc_f16(64, 16, BF16, true, true), k > 0);
+                gemm(tmem, kmaj(tG5, 128), mnmaj(sW5, 16), 1, idesc_f16(128, 64, BF16, false, true), false);
+                mma_commit(&bar);
+            }
+            wait_mma(&bar, phase, timed_out);
+            mask_epilogue<BF16>(trow, tH4, r, m4a, m4b);                 // G4
+            // dW4 += G4^T H3 ; dH3 = G4 W4
+            to_tensor_mlp();
+            if (r == 0) {
+                gemm(tmem + kColW4, mnmaj(tH4, 128), mnmaj(tH3, 128), 8, idesc_f16(64, 64, BF16, true, true), k > 0);
+                gemm(tmem, kmaj(tH4, 128), mnmaj(sW4, 64), 4, idesc_f16(128, 64, BF16, false, true), false);
+                mma_commit(&bar);
+            }
+            wait_mma(&bar, phase, timed_out);
+            mask_epilogue<BF16>(trow, tH3, r, m3a, m3b);                 // G3
+            // dW3 += G3^T X3 ; dX3 = G3 W3
+            to_tensor_mlp();
+            if (r == 0) {
+                gemm(tmem + kColW3, mnmaj(tH3, 128), mnmaj(tX3, 128), 8, idesc_f16(64, 32, BF16, true, true), k > 0);
+                gemm(tmem, kmaj(tH3, 128), mnmaj(sW3, 64), 4, idesc_f16(128, 32, BF16, false, true), false);
+                mma_commit(&bar);
+            }
+            wait_mma(&bar, phase, timed_out);
+            ld_cols<16>(trow, 0, v);
+            v[0] += S * rz.w * sigma;                                    // dL/dh_0 += dL/dsigma * sigma
+            store_row_at<BF16, 16>(tX3, r, 0, v);                        // G2 (columns 0..15)
+            // dW2^T += H1^T G2 ; dH1 = G2 W2
+            to_tensor_mlp();
+            if (r == 0) {
+                gemm(tmem + kColW2T, mnmaj(tH1, 128), mnmaj(tX3, 128), 8, idesc_f16(64, 16, BF16, true, true),
+                     k > 0);
+                gemm(tmem, kmaj(tX3, 128), mnmaj(sW2, 16), 1, idesc_f16(128, 64, BF16, false, true), false);
+                mma_commit(&bar);
+            }
+            wait_mma(&bar, phase, timed_out);
+            mask_epilogue<BF16>(trow, tH1, r, m1a, m1b);                 // G1
+            // dW1 += G1^T X0 ; dF = G1 W1
+            to_tensor_mlp();
+            if (r == 0) {
+                gemm(tmem + kColW1, mnmaj(tH1, 128), mnmaj(tX0, 128), 8, idesc_f16(64, 32, BF16, true, true), k > 0);
+                gemm(tmem, kmaj(tH1, 128), mnmaj(sW1, 64), 4, idesc_f16(128, 32, BF16, false, true), false);
+                mma_commit(&bar);
+            }
+            wait_mma(&bar, phase, timed_out);
+            ld_cols<32>(trow, 0, v);
+            fence_before_sync();
+            if (k > 0) nb_sync(kBarDfFree, 256);          // the IO group has read the previous tile's rows
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = ((k < 32 ? (m4a >> k) : (m4b >> (k - 32))) & 1u) ? v[k] : 0.f;
-        store_row<BF16, 64>(tH4, tid, v);                       // G4
-        // dW4 += G4^T H3 ; dH3 = G4 W4
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem + kColW4, mnmaj(tH4, 128), mnmaj(tH3, 128), 8, idesc_f16(64, 64, BF16, true, true), !first);
-            gemm(tmem, kmaj(tH4, 128), mnmaj(sW4, 64), 4, idesc_f16(128, 64, BF16, false, true), false);
-            mma_commit(&bar);
+            for (int q = 0; q < 8; ++q)
+                *reinterpret_cast<float4*>(sDf + df_offset(r, q)) =
+                    make_float4(v[4 * q] * inv_S, v[4 * q + 1] * inv_S, v[4 * q + 2] * inv_S, v[4 * q + 3] * inv_S);
+            nb_arrive(kBarDfReady, 256);                  // also: X0 and the row data are free
         }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<64>(trow, 0, v);
+        // ---- flush the weight gradients (lane 32*(m/16) + m%16 holds row m)
+        const bool any_timeout = __syncthreads_or(timed_out) != 0;  // both groups take part
+        fence_after_sync();
+        if (timed_out) mbar_wait(&bar, phase ^ 1u, kWaitPolls);
+        if (n_mine > 0 && !any_timeout) {
+            float* gm_ = grads + (size_t)c.L * c.T * 2;
+            const int lane = tid & 31;
+            const int m = warp * 16 + lane;
+            const bool has = lane < 16;
+            float w[32];
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = ((k < 32 ? (m3a >> k) : (m3b >> (k - 32))) & 1u) ? v[k] : 0.f;
-        store_row<BF16, 64>(tH3, tid, v);                       // G3
-        // dW3 += G3^T X3 ; dX3 = G3 W3
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem + kColW3, mnmaj(tH3, 128), mnmaj(tX3, 128), 8, idesc_f16(64, 32, BF16, true, true), !first);
-            gemm(tmem, kmaj(tH3, 128), mnmaj(sW3, 64), 4, idesc_f16(128, 32, BF16, false, true), false);
-            mma_commit(&bar);
+            for (int h = 0; h < 2; ++h) {
+                ld_cols<32>(trow, kColW4 + 32 * h, w);
+                if (has)
+                    for (int q = 0; q < 32; ++q) atomicAdd(gm_ + kOffW4 + m * 64 + 32 * h + q, w[q] * inv_S);
+            }
+            ld_cols<32>(trow, kColW3, w);
+            if (has)
+                for (int q = 0; q < 32; ++q) atomicAdd(gm_ + kOffW3 + m * 32 + q, w[q] * inv_S);
+            ld_cols<32>(trow, kColW1, w);
+            if (has)
+                for (int q = 0; q < 32; ++q) atomicAdd(gm_ + kOffW1 + m * 32 + q, w[q] * inv_S * inv_fs);
+            ld_cols<16>(trow, kColW2T, w);
+            if (has)
+                for (int q = 0; q < 16; ++q) atomicAdd(gm_ + kOffW2 + q * 64 + m, w[q] * inv_S);
+            ld_cols<16>(trow, kColW5T, w);
+            if (has)
+                for (int q = 0; q < 3; ++q) atomicAdd(gm_ + kOffW5 + q * 64 + m, w[q] * inv_S);
         }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<16>(trow, 0, v);
-        v[0] += S * g.x * sigma;                                // dL/dh_0 += dL/dsigma * sigma
-        store_row<BF16, 16>(tX3, tid, v);                       // G2 (columns 0..15)
-        // dW2^T += H1^T G2 ; dH1 = G2 W2
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem + kColW2T, mnmaj(tH1, 128), mnmaj(tX3, 128), 8, idesc_f16(64, 16, BF16, true, true), !first);
-            gemm(tmem, kmaj(tX3, 128), mnmaj(sW2, 16), 1, idesc_f16(128, 64, BF16, false, true), false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<64>(trow, 0, v);
+        if (any_timeout && tid == 0) atomicOr(err, kErrTimeout);
+    } else {
+        // ======================= IO group: tile inputs one tile ahead, gradient scatter
+        float2* gtables = reinterpret_cast<float2*>(grads);
+        float3 x_cur = make_float3(0.f, 0.f, 0.f), x_next = x_cur;
+        bool valid_cur = false, valid_next = false;
+        uint4 f_next[4];
+        float4 rd_next, rz_next;
+        // inputs of this block's k-th tile for row r, into registers
+        auto load = [&](uint32_t k) {
+            const uint32_t i = (blockIdx.x + k * gridDim.x) * 128 + r;
+            valid_next = i < n;
+            float3 d = make_float3(0.f, 0.f, 0.f);
+            x_next = make_float3(0.f, 0.f, 0.f);
+            rd_next = make_float4(0.f, 0.f, 0.f, 0.f);
+            rz_next = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = ((k < 32 ? (m1a >> k) : (m1b >> (k - 32))) & 1u) ? v[k] : 0.f;
-        store_row<BF16, 64>(tH1, tid, v);                       // G1
-        // dW1 += G1^T X0 ; dF = G1 W1
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem + kColW1, mnmaj(tH1, 128), mnmaj(tX0, 128), 8, idesc_f16(64, 32, BF16, true, true), !first);
-            gemm(tmem, kmaj(tH1, 128), mnmaj(sW1, 64), 4, idesc_f16(128, 32, BF16, false, true), false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out);
-        ld_cols<32>(trow, 0, v);
+            for (int q = 0; q < 4; ++q) f_next[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (valid_next) {
+                x_next = sample_pos_tc(c, rays, cap, ray_id[i], ts[i], d);
+                const float4 g = dsig_rgb[i], col = sig_rgb[i];
 #pragma unroll
-        for (int k = 0; k < kEnc; ++k) v[k] *= inv_S;
-        hash_scatter_warp(c, gtables, x, v, valid && !timed_out);
-        first = false;
-        fence_before_sync();
-        if (__syncthreads_or(timed_out)) {
-            if (tid == 0) atomicOr(err, kErrTimeout);
-            break;
+                for (int q = 0; q < 4; ++q) f_next[q] = feat[(size_t)i * 4 + q];
+                rd_next = make_float4(d.x, d.y, d.z, 1.f);
+                rz_next = make_float4(S * g.y * col.y * (1.f - col.y), S * g.z * col.z * (1.f - col.z),
+                                      S * g.w * col.w * (1.f - col.w), g.x);
+            }
+        };
+        auto publish = [&]() {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(tX0 + tile_offset(r, 8 * q, 128)) = f_next[q];
+            sRow[2 * r] = rd_next;
+            sRow[2 * r + 1] = rz_next;
+            x_cur = x_next;
+            valid_cur = valid_next;
+            fence_proxy_async();                      // X0 is read by the tensor core
+            nb_arrive(kBarIn, 256);
+        };
+        if (n_mine > 0) {
+            load(0);
+            publish();
         }
-    }
-    fence_before_sync();
-    const bool any_timeout = __syncthreads_or(timed_out);
-    fence_after_sync();
-    if (timed_out) mbar_wait(&bar, phase ^ 1u, kWaitPolls);
-    // ---- flush the weight gradients (lane 32*(m/16) + m%16 holds row m)
-    if (!first && !any_timeout) {
-        float* gm = grads + (size_t)c.L * c.T * 2;
-        const int lane = tid & 31;
-        const int m = warp * 16 + lane;
-        const bool has = lane < 16;
-        float w[64];
-        ld_cols<64>(trow, kColW4, w);
-        if (has)
-            for (int k = 0; k < 64; ++k) atomicAdd(gm + kOffW4 + m * 64 + k, w[k] * inv_S);
-        ld_cols<32>(trow, kColW3, w);
-        if (has)
-            for (int k = 0; k < 32; ++k) atomicAdd(gm + kOffW3 + m * 32 + k, w[k] * inv_S);
-        ld_cols<32>(trow, kColW1, w);
-        if (has)
-            for (int k = 0; k < 32; ++k) atomicAdd(gm + kOffW1 + m * 32 + k, w[k] * inv_S * inv_fs);
-        ld_cols<16>(trow, kColW2T, w);
-        if (has)
-            for (int k = 0; k < 16; ++k) atomicAdd(gm + kOffW2 + k * 64 + m, w[k] * inv_S);
-        ld_cols<16>(trow, kColW5T, w);
-        if (has)
-            for (int k = 0; k < 3; ++k) atomicAdd(gm + kOffW5 + k * 64 + m, w[k] * inv_S);
+        for (uint32_t k = 0; k < n_mine; ++k) {
+            if (k + 1 < n_mine) load(k + 1);          // global loads in flight during the chain
+            nb_sync(kBarDfReady, 256);
+            const float3 x_done = x_cur;
+            const bool valid_done = valid_cur;
+            float v[32];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 a = *reinterpret_cast<const float4*>(sDf + df_offset(r, q));
+                v[4 * q] = a.x;
+                v[4 * q + 1] = a.y;
+                v[4 * q + 2] = a.z;
+                v[4 * q + 3] = a.w;
+            }
+            if (k + 1 < n_mine) publish();            // next tile's inputs; the MLP group starts on it
+            if (k + 1 < n_mine) nb_arrive(kBarDfFree, 256);
+            hash_scatter_warp(c, gtables, x_done, v, valid_done);
+        }
+        __syncthreads_or(false);                      // pairs with the MLP group's flush barrier
     }
     fence_before_sync();
     __syncthreads();
@@ -556,7 +656,7 @@ static void bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t 
         attr = true;
     }
     const float fs = BF16 ? 1.f : 256.f;
-    k_field_bwd_tc<BF16><<<n_sm * 2, 128, kBwdSmem, s>>>(c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays,
+    k_field_bwd_tc<BF16><<<n_sm * 2, 256, kBwdSmem, s>>>(c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays,
                                                           b.ray_id, b.t, reinterpret_cast<const uint4*>(b.feat),
                                                           b.sig_rgb, b.dsig_rgb, fs, b.loss, b.err);
 }
