@@ -192,7 +192,10 @@ const float* map_loss_device(map_handle h);
  * floats, out_depth: H*W floats (expected ray-termination distance along the unit
  * ray), both in mem_kind memory; either may be NULL.  out_acc (nullable, same
  * memory kind): H*W accumulated opacities.  Rays stop once transmittance drops
- * below cfg.render_t_min.
+ * below cfg.render_t_min.  Views of more than max(2^18, the map's current ray
+ * capacity) pixels are rendered in chunks of that many pixels (map_get_samples and
+ * map_get_ray_outputs then describe the last chunk).  With host outputs the call
+ * waits for the stream; with device outputs it returns once the work is queued.
  */
 int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, uint32_t H,
                float* out_rgb, float* out_depth, float* out_acc, int mem_kind, void* stream);
@@ -285,6 +288,83 @@ int map_march_noalloc(const map_config* cfg, const uint8_t* occ_bits, const floa
  */
 int map_probe_random_access(float* table, uint64_t n_entries, uint32_t n_threads, uint32_t per_thread,
                             int mode, uint64_t seed, float* sink, void* stream);
+
+/*
+ * Serving: several maps resident on one GPU (Sec. 3.3's mapping thread, which
+ * optimises continuously while keyframes arrive and renders are requested, run for
+ * several scenes at once).  A server owns a worker thread; each admitted scene gets
+ * its own map and CUDA stream.  Requests of one scene run in submission order, up to
+ * max_inflight of them on the GPU at a time; requests arriving meanwhile join
+ * between them, and different scenes' work overlaps on the device.  A scene with
+ * continuous mapping fills every gap in its queue with a mapping step of step_rays
+ * rays.  Scenes are admitted while the device's free memory covers the scene's
+ * estimated footprint (tables, gradients, Adam moments, occupancy, step workspace,
+ * kf_reserve_bytes of keyframes) plus hbm_reserve_bytes; otherwise the call returns
+ * MAP_ENOMEM and may be retried once scenes have been removed or memory freed.
+ */
+typedef struct map_server_s* map_server;
+
+#define MAP_REQ_KEYFRAME 0
+#define MAP_REQ_STEP 1
+#define MAP_REQ_RENDER 2
+
+typedef struct map_server_config {
+    uint32_t max_scenes;        /* scene slots, 1..64 */
+    uint32_t max_inflight;      /* requests per scene on the GPU at once (>= 1) */
+    uint32_t step_rays;         /* rays of a continuous-mapping step */
+    uint32_t reserved0;
+    size_t hbm_reserve_bytes;   /* device memory left free at admission */
+    size_t kf_reserve_bytes;    /* keyframe memory budgeted per scene */
+    uint64_t seed;              /* reserved (each scene draws its rays from its map_config seed) */
+} map_server_config;
+
+/* One finished request.  Times are seconds since map_server_create.  A keyframe
+ * is done when the first mapping step that can draw from it has completed (its
+ * insertion, if the scene has no continuous mapping); step_index is that step
+ * (keyframe) or the step's own index; loss is the step's L_M when requested. */
+typedef struct map_completion {
+    uint64_t req_id;
+    uint64_t step_index;
+    uint32_t scene;
+    uint32_t kind;
+    int32_t status;
+    float loss;
+    double t_submit;
+    double t_start;
+    double t_done;
+} map_completion;
+
+typedef struct map_server_stats {
+    double t_now;
+    uint64_t rays_done;     /* rays of all completed mapping steps */
+    uint64_t steps_done;
+    uint64_t device_bytes;  /* admitted scenes' estimated footprints */
+    uint32_t n_scenes;
+    uint32_t pending;       /* requests submitted and not yet polled */
+} map_server_stats;
+
+int map_server_create(const map_server_config* cfg, map_server* out);
+/* Stops the worker, waits for the device and frees every scene. */
+int map_server_destroy(map_server s);
+/* Admission by free HBM (see above); cfg as for map_create. */
+int map_server_add_scene(map_server s, const map_config* cfg, int continuous_mapping, uint32_t* scene_id);
+/* The scene's map, for parameter and occupancy I/O while no request of the scene
+ * is pending (the worker thread owns it otherwise). */
+int map_server_scene_handle(map_server s, uint32_t scene, map_handle* out);
+/* Copies the keyframe (host memory) before returning; semantics of map_add_keyframe. */
+int map_server_submit_keyframe(map_server s, uint32_t scene, uint32_t kf_id, const float c2w[12],
+                               const float K[4], uint32_t W, uint32_t H, const float* rgb, const float* depth,
+                               const float* depth_var, int depth_is_z, uint64_t* req_id);
+/* One mapping step of n_rays rays; want_loss: report L_M in the completion. */
+int map_server_submit_step(map_server s, uint32_t scene, uint32_t n_rays, int want_loss, uint64_t* req_id);
+/* Render into host buffers out_rgb (H*W*3) and out_depth (H*W), either may be
+ * NULL; they must stay valid until the request's completion has been polled (the
+ * poll writes them). */
+int map_server_submit_render(map_server s, uint32_t scene, const float c2w[12], const float K[4], uint32_t W,
+                             uint32_t H, float* out_rgb, float* out_depth, uint64_t* req_id);
+/* Up to cap finished requests, oldest first. */
+int map_server_poll(map_server s, map_completion* out, uint32_t cap, uint32_t* n_out);
+int map_server_get_stats(map_server s, map_server_stats* out);
 
 /* sizeof(map_config) as compiled into the library, so a binding can check that its
  * own copy of the struct has the same layout. */

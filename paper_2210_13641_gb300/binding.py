@@ -56,6 +56,26 @@ class MapStats(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_scenes", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
+                ("step_rays", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("hbm_reserve_bytes", ctypes.c_size_t), ("kf_reserve_bytes", ctypes.c_size_t),
+                ("seed", ctypes.c_uint64)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("step_index", ctypes.c_uint64), ("scene", ctypes.c_uint32),
+                ("kind", ctypes.c_uint32), ("status", ctypes.c_int32), ("loss", ctypes.c_float),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("t_now", ctypes.c_double), ("rays_done", ctypes.c_uint64), ("steps_done", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("n_scenes", ctypes.c_uint32), ("pending", ctypes.c_uint32)]
+
+
+REQ_KEYFRAME, REQ_STEP, REQ_RENDER = 0, 1, 2
+
 PHASES = ["ray_gen", "march", "field_fwd", "composite", "field_bwd", "adam", "occupancy", "output"]
 
 
@@ -87,6 +107,23 @@ _SIGS = {
                                            ctypes.c_size_t, ctypes.c_void_p]),
     "map_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MapStats)]),
     "map_abi_config_size": (ctypes.c_size_t, []),
+    "map_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    "map_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "map_server_add_scene": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MapConfig), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_uint32)]),
+    "map_server_scene_handle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
+    "map_server_submit_keyframe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "map_server_submit_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_uint64)]),
+    "map_server_submit_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.POINTER(ctypes.c_uint64)]),
+    "map_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                       ctypes.POINTER(ctypes.c_uint32)]),
+    "map_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
     "map_probe_random_access": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "map_march_noalloc": (ctypes.c_int, [ctypes.POINTER(MapConfig), ctypes.c_void_p, ctypes.c_void_p,
@@ -395,3 +432,120 @@ class NerfMap:
         self._check(self.lib.map_get_ray_outputs(self.h, rgb.ctypes.data, d.ctypes.data, a.ctypes.data, n_rays,
                                                  None))
         return rgb, d, a
+
+
+class MapServer:
+    """Multi-scene serving loop (map_server_* of the C ABI)."""
+
+    def __init__(self, max_scenes=4, max_inflight=2, step_rays=1 << 18, hbm_reserve=1 << 30,
+                 kf_reserve=1 << 30, seed=0):
+        self.lib = load()
+        c = ServerConfig(max_scenes, max_inflight, step_rays, 0, hbm_reserve, kf_reserve, seed)
+        h = ctypes.c_void_p()
+        rc = self.lib.map_server_create(ctypes.byref(c), ctypes.byref(h))
+        if rc != MAP_OK:
+            raise MapError(rc, "map_server_create failed")
+        self.h = h
+        self._keep = {}          # render output buffers, alive until polled
+        self._done = {}          # polled completions not yet handed out by wait()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.map_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_scene(self, cfg, continuous_mapping=True, occ_every=0):
+        ccfg = make_config(cfg, occ_every)
+        sid = ctypes.c_uint32()
+        rc = self.lib.map_server_add_scene(self.h, ctypes.byref(ccfg), int(continuous_mapping), ctypes.byref(sid))
+        if rc != MAP_OK:
+            raise MapError(rc, "scene not admitted" if rc == MAP_ENOMEM else "add_scene failed")
+        return sid.value
+
+    def scene_map(self, scene, cfg):
+        """A NerfMap view of the scene's map (for parameter / occupancy I/O while the
+        scene has no pending request); it does not own the map."""
+        h = ctypes.c_void_p()
+        rc = self.lib.map_server_scene_handle(self.h, scene, ctypes.byref(h))
+        if rc != MAP_OK:
+            raise MapError(rc, "bad scene")
+        m = NerfMap.__new__(NerfMap)
+        m.lib, m.cfg, m.h = self.lib, cfg, h
+        m.n_params = m.stats().param_count
+        m.close = lambda: None
+        return m
+
+    def submit_keyframe(self, scene, kf):
+        rid = ctypes.c_uint64()
+        c2w = np.ascontiguousarray(kf.c2w, np.float32).reshape(12)
+        K = np.ascontiguousarray(kf.K, np.float32).reshape(4)
+        rgb = np.ascontiguousarray(kf.rgb, np.float32)
+        dep = np.ascontiguousarray(kf.depth, np.float32)
+        var = np.ascontiguousarray(kf.var, np.float32)
+        rc = self.lib.map_server_submit_keyframe(self.h, scene, kf.kf_id, c2w.ctypes.data, K.ctypes.data, kf.W,
+                                                 kf.H, rgb.ctypes.data, dep.ctypes.data, var.ctypes.data,
+                                                 int(bool(kf.depth_is_z)), ctypes.byref(rid))
+        if rc != MAP_OK:
+            raise MapError(rc, "submit_keyframe failed")
+        return rid.value
+
+    def submit_step(self, scene, n_rays, want_loss=True):
+        rid = ctypes.c_uint64()
+        rc = self.lib.map_server_submit_step(self.h, scene, n_rays, int(want_loss), ctypes.byref(rid))
+        if rc != MAP_OK:
+            raise MapError(rc, "submit_step failed")
+        return rid.value
+
+    def submit_render(self, scene, c2w, K, W, H):
+        """Returns (request id, rgb [H,W,3], depth [H,W]); the arrays are filled when
+        the request's completion is polled."""
+        rid = ctypes.c_uint64()
+        c2w = np.ascontiguousarray(c2w, np.float32).reshape(12)
+        K = np.ascontiguousarray(K, np.float32).reshape(4)
+        rgb = np.zeros((H, W, 3), np.float32)
+        dep = np.zeros((H, W), np.float32)
+        rc = self.lib.map_server_submit_render(self.h, scene, c2w.ctypes.data, K.ctypes.data, W, H,
+                                               rgb.ctypes.data, dep.ctypes.data, ctypes.byref(rid))
+        if rc != MAP_OK:
+            raise MapError(rc, "submit_render failed")
+        self._keep[rid.value] = (rgb, dep)
+        return rid.value, rgb, dep
+
+    def poll(self, cap=256):
+        buf = (Completion * cap)()
+        n = ctypes.c_uint32()
+        rc = self.lib.map_server_poll(self.h, buf, cap, ctypes.byref(n))
+        if rc != MAP_OK:
+            raise MapError(rc, "poll failed")
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            self._keep.pop(c.req_id, None)
+            out.append({"id": c.req_id, "scene": c.scene, "kind": c.kind, "status": c.status,
+                        "step_index": c.step_index, "loss": c.loss, "t_submit": c.t_submit,
+                        "t_start": c.t_start, "t_done": c.t_done})
+        return out
+
+    def wait(self, ids, timeout=120.0):
+        """Polls until every request in `ids` has completed; returns their records."""
+        import time
+        want = set(ids)
+        t0 = time.time()
+        while want - set(self._done):
+            for c in self.poll():
+                self._done[c["id"]] = c
+            if time.time() - t0 > timeout:
+                raise TimeoutError(f"requests not done: {sorted(want - set(self._done))[:5]}")
+            time.sleep(0.0005)
+        return {i: self._done.pop(i) for i in ids}
+
+    def stats(self):
+        st = ServerStats()
+        self.lib.map_server_get_stats(self.h, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}

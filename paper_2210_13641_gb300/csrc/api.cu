@@ -229,6 +229,8 @@ int check_launch(map_scene* h, const char* what) {
     return MAP_OK;
 }
 
+constexpr uint32_t kRenderChunk = 1u << 18;
+
 const char* const kPhaseName[MAP_PHASES] = {"ray_gen", "march", "field_fwd", "composite",
                                              "field_bwd", "adam", "occupancy", "output"};
 
@@ -349,8 +351,9 @@ int map_add_keyframe(map_handle h, uint32_t kf_id, const float c2w[12], const fl
             // drop the entry (new, or replaced at a new size) and republish the table
             h->kfs.erase(h->kfs.begin() + idx);
             if (idx < h->kf_desc.size()) h->kf_desc.erase(h->kf_desc.begin() + idx);
-            if (h->d_kfs && !h->kf_desc.empty())
-                copy_in(h, h->d_kfs, h->kf_desc.data(), h->kf_desc.size() * sizeof(KfDesc), MAP_MEM_HOST, s);
+            if (h->d_kfs)
+                for (size_t i = 0; i < h->kf_desc.size(); ++i)
+                    launch_set_kf_desc(h->d_kfs, (uint32_t)i, h->kf_desc[i], s);
             return fail(h, rc, h->err);
         }
         kf.bytes = npx * 2 * sizeof(float4);
@@ -386,6 +389,7 @@ int map_add_keyframe(map_handle h, uint32_t kf_id, const float c2w[12], const fl
     if (h->kf_desc.size() <= idx) h->kf_desc.resize(idx + 1);
     h->kf_desc[idx] = dsc;
     if (h->d_kfs_cap < h->kf_desc.size()) {
+        // grow the device table: rewrite every descriptor into the new one
         cudaStreamSynchronize(s);
         dfree(h, h->d_kfs);
         h->d_kfs = nullptr;
@@ -393,9 +397,11 @@ int map_add_keyframe(map_handle h, uint32_t kf_id, const float c2w[12], const fl
         rc = dalloc(h, (void**)&h->d_kfs, cap * sizeof(KfDesc));
         if (rc) return rc;
         h->d_kfs_cap = cap;
+        for (size_t i = 0; i < h->kf_desc.size(); ++i) launch_set_kf_desc(h->d_kfs, (uint32_t)i, h->kf_desc[i], s);
+    } else {
+        launch_set_kf_desc(h->d_kfs, (uint32_t)idx, dsc, s);
     }
-    // pageable source: staged before the call returns, so kf_desc may change afterwards
-    return copy_in(h, h->d_kfs, h->kf_desc.data(), h->kf_desc.size() * sizeof(KfDesc), MAP_MEM_HOST, s);
+    return check_launch(h, "keyframe table");
 }
 
 static int run_forward(map_scene* h, uint32_t n_rays, bool train, cudaStream_t s) {
@@ -476,28 +482,43 @@ int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, 
     cudaStream_t s = (cudaStream_t)stream;
     h->last_stream = s;
     const uint32_t n = W * H;
-    int rc = ensure_step_bufs(h, n);
+    // views larger than the work buffers (or than 2^18 rays) are rendered in chunks
+    const uint32_t chunk = std::min<uint32_t>(n, std::max<uint32_t>(h->bufs.cap_rays, kRenderChunk));
+    int rc = ensure_step_bufs(h, chunk);
     if (rc) return rc;
     const StepBufs& b = h->bufs;
-    rc = phase(h, MAP_PH_RAYGEN, 1, s, [&] { launch_ray_gen_view(c2w, K, W, H, b, s); });
-    if (!rc) rc = run_forward(h, n, false, s);
-    if (rc) return rc;
     DevCfg dc = h->dc;
     dc.t_min = h->cfg.render_t_min;
-    rc = phase(h, MAP_PH_COMPOSITE, 1, s, [&] { launch_composite(dc, n, false, b, s); });
-    if (rc) return rc;
-    h->last_rays = n;
-    if (mem_kind == MAP_MEM_DEVICE)
-        return phase(h, MAP_PH_OUTPUT, 1, s, [&] { launch_write_render(b, n, out_rgb, out_depth, out_acc, s); });
-    // host outputs: interleave into the feature buffer (unused by a render), then copy
-    float* tmp = b.feat;
-    rc = phase(h, MAP_PH_OUTPUT, 1, s,
-               [&] { launch_write_render(b, n, tmp, tmp + 3 * (size_t)n, tmp + 4 * (size_t)n, s); });
-    if (rc) return rc;
-    if (out_rgb) NM_CUDA(h, cudaMemcpyAsync(out_rgb, tmp, 3 * (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
-    if (out_depth) NM_CUDA(h, cudaMemcpyAsync(out_depth, tmp + 3 * (size_t)n, n * sizeof(float), cudaMemcpyDeviceToHost, s));
-    if (out_acc) NM_CUDA(h, cudaMemcpyAsync(out_acc, tmp + 4 * (size_t)n, n * sizeof(float), cudaMemcpyDeviceToHost, s));
-    NM_CUDA(h, cudaStreamSynchronize(s));
+    float* tmp = b.feat;  // host outputs: staged here (unused by a render), then copied
+    for (uint32_t p0 = 0; p0 < n; p0 += chunk) {
+        const uint32_t cnt = std::min(chunk, n - p0);
+        rc = phase(h, MAP_PH_RAYGEN, 1, s, [&] { launch_ray_gen_view(c2w, K, W, p0, cnt, b, s); });
+        if (!rc) rc = run_forward(h, cnt, false, s);
+        if (!rc) rc = phase(h, MAP_PH_COMPOSITE, 1, s, [&] { launch_composite(dc, cnt, false, b, s); });
+        if (rc) return rc;
+        h->last_rays = cnt;
+        if (mem_kind == MAP_MEM_DEVICE) {
+            rc = phase(h, MAP_PH_OUTPUT, 1, s, [&] {
+                launch_write_render(b, cnt, out_rgb ? out_rgb + 3 * (size_t)p0 : nullptr,
+                                    out_depth ? out_depth + p0 : nullptr, out_acc ? out_acc + p0 : nullptr, s);
+            });
+            if (rc) return rc;
+            continue;
+        }
+        rc = phase(h, MAP_PH_OUTPUT, 1, s,
+                   [&] { launch_write_render(b, cnt, tmp, tmp + 3 * (size_t)cnt, tmp + 4 * (size_t)cnt, s); });
+        if (rc) return rc;
+        if (out_rgb)
+            NM_CUDA(h, cudaMemcpyAsync(out_rgb + 3 * (size_t)p0, tmp, 3 * (size_t)cnt * sizeof(float),
+                                       cudaMemcpyDeviceToHost, s));
+        if (out_depth)
+            NM_CUDA(h, cudaMemcpyAsync(out_depth + p0, tmp + 3 * (size_t)cnt, cnt * sizeof(float),
+                                       cudaMemcpyDeviceToHost, s));
+        if (out_acc)
+            NM_CUDA(h, cudaMemcpyAsync(out_acc + p0, tmp + 4 * (size_t)cnt, cnt * sizeof(float),
+                                       cudaMemcpyDeviceToHost, s));
+        NM_CUDA(h, cudaStreamSynchronize(s));  // the staging buffer is reused by the next chunk
+    }
     return MAP_OK;
 }
 

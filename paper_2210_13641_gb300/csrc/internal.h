@@ -39,12 +39,13 @@ struct StepBufs {
 };
 
 // k_rays.cu
+void launch_set_kf_desc(KfDesc* table, uint32_t idx, const KfDesc& d, cudaStream_t s);
 void launch_keyframe_texels(const float* rgb, const float* depth, const float* var, uint32_t W,
                             uint32_t H, const float* K, int depth_is_z, float4* texels,
                             cudaStream_t s);
 void launch_ray_gen(const KfDesc* kfs, uint32_t n_kf, uint64_t seed, uint64_t step,
                     uint32_t n_rays, const StepBufs& b, cudaStream_t s);
-void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t H,
+void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t p0, uint32_t cnt,
                          const StepBufs& b, cudaStream_t s);
 void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, const StepBufs& b,
                   cudaStream_t s);

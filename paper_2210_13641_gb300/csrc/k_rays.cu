@@ -27,6 +27,14 @@ __global__ void k_keyframe_texels(const float* __restrict__ rgb, const float* __
     tex[2 * p + 1] = make_float4(V, 0.f, 0.f, 0.f);
 }
 
+// Writes one keyframe descriptor into the device table (stream ordered; the
+// descriptor travels as a kernel argument, so no host buffer has to outlive the call).
+__global__ void k_set_kf_desc(KfDesc* __restrict__ table, uint32_t idx, KfDesc d) { table[idx] = d; }
+
+void launch_set_kf_desc(KfDesc* table, uint32_t idx, const KfDesc& d, cudaStream_t s) {
+    k_set_kf_desc<<<1, 1, 0, s>>>(table, idx, d);
+}
+
 void launch_keyframe_texels(const float* rgb, const float* depth, const float* var, uint32_t W,
                             uint32_t H, const float* K, int depth_is_z, float4* texels,
                             cudaStream_t s) {
@@ -94,22 +102,23 @@ struct ViewCam {
     float K[4];
 };
 
-__global__ void k_ray_gen_view(ViewCam cam, uint32_t W, uint32_t H, float* __restrict__ rays,
+// Rays of pixels p0 .. p0 + cnt - 1 of a W-wide view (row-major), as rays 0 .. cnt - 1.
+__global__ void k_ray_gen_view(ViewCam cam, uint32_t W, uint32_t p0, uint32_t cnt, float* __restrict__ rays,
                                uint32_t cap) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= W * H) return;
+    if (r >= cnt) return;
+    const uint32_t pix = p0 + r;
     float3 o, d;
-    cast_ray(cam.c2w, cam.K, r % W, r / W, o, d);
+    cast_ray(cam.c2w, cam.K, pix % W, pix / W, o, d);
     store_ray(rays, cap, r, o, d, make_float4(0.f, 0.f, 0.f, 0.f), 1.f);
 }
 
-void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t H,
+void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t p0, uint32_t cnt,
                          const StepBufs& b, cudaStream_t s) {
     ViewCam cam;
     for (int i = 0; i < 12; ++i) cam.c2w[i] = c2w[i];
     for (int i = 0; i < 4; ++i) cam.K[i] = K[i];
-    const uint32_t n = W * H;
-    k_ray_gen_view<<<(n + 255) / 256, 256, 0, s>>>(cam, W, H, b.rays, b.cap_rays);
+    k_ray_gen_view<<<(cnt + 255) / 256, 256, 0, s>>>(cam, W, p0, cnt, b.rays, b.cap_rays);
 }
 
 // ---------------------------------------------------------------- march

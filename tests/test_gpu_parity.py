@@ -248,3 +248,23 @@ def test_full_size_room_step_sampled(room_workload):
     per_ray = ((I - rgb) ** 2).sum(1) + float(cfg.lambda_d) * (Dt - D) ** 2 / V
     assert loss == pytest.approx(per_ray.mean(), rel=REL)
     assert counts.mean() > 5
+
+
+def test_render_in_chunks_matches_oracle_on_sampled_pixels():
+    """A 600x450 view (270k pixels, more than one 2^18-ray chunk): pixels on both
+    sides of the chunk boundary equal the oracle's forward on the same rays."""
+    cfg = synth.config_small(occ_res=0, render_t_min=np.float32(0.0))
+    P = synth.random_params(cfg, 21, table_scale=0.5, mlp_std=0.3)
+    m = _map(cfg, P, [synth.c1_keyframe(0, W=8, H=8)])
+    W, H = 600, 450
+    kf = synth.c1_keyframe(22, W=W, H=H)
+    kf.K = np.array([400.0, 400.0, 300.0, 225.0], np.float32)
+    rgb, D, acc = m.render(kf.c2w, kf.K, W, H)
+    pix = np.concatenate([np.arange((1 << 18) - 300, (1 << 18) + 300),
+                          np.random.default_rng(23).choice(W * H, 400, replace=False)])
+    v, u = np.divmod(pix, W)
+    ref = oracle.forward_backward(cfg, P, [kf], len(pix), 0, 0, rays=(np.zeros(len(pix), int), u, v),
+                                  want_grad=False)
+    assert np.allclose(rgb.reshape(-1, 3)[pix], ref["I_hat"], rtol=REL, atol=1e-6)
+    assert np.allclose(D.ravel()[pix], ref["D_hat"], rtol=REL, atol=1e-6)
+    assert np.allclose(acc.ravel()[pix], ref["acc"], rtol=REL, atol=1e-6)
