@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"])
     p.add_argument("--no-forms", action="store_true", help="skip timing the other MLP precisions")
+    p.add_argument("--no-serving", action="store_true", help="skip the multi-scene serving measurement")
+    p.add_argument("--serving-seconds", type=float, default=6.0)
     p.add_argument("--rays", type=int, default=N_RAYS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
@@ -170,6 +172,82 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- serving
+
+def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0):
+    """Four resident scenes (tables 2^16 .. 2^19 per level, the room workload) with
+    continuous mapping (2^16-ray steps), each receiving a 640x480 keyframe at 10 Hz,
+    plus render queries (160x120, 640x480, 1280x720) arriving as a Poisson stream of
+    30 per second over random scenes.  Returns p50/p99 latencies and the aggregate
+    mapping rays/s of the window."""
+    import numpy as np
+    import synth
+    from paper_2210_13641_gb300 import pack_params
+    from paper_2210_13641_gb300.binding import MapServer
+    rng = np.random.default_rng(seed)
+    server = MapServer(max_scenes=4, max_inflight=2, step_rays=1 << 16)
+    scenes = []
+    for j, log2t in enumerate((16, 17, 18, 19)):
+        cfg = synth.config_c2(precision=precision, log2_table=log2t, seed=j)
+        sid = server.add_scene(cfg, continuous_mapping=True)
+        sm = server.scene_map(sid, cfg)
+        sm.set_params(pack_params(synth.random_params(cfg, j)))
+        sm.set_occupancy(bits)
+        scenes.append(sid)
+    warm = [server.submit_keyframe(sid, kfs[i]) for sid in scenes for i in range(4)]
+    server.wait(warm, timeout=300)
+    time.sleep(0.5)
+    res = [(160, 120), (640, 480), (1280, 720)]
+    events = []
+    for j, sid in enumerate(scenes):                      # keyframes at 10 Hz per scene
+        t = 0.025 * j
+        while t < seconds:
+            events.append((t, "kf", sid))
+            t += 0.1
+    t = 0.0
+    while True:                                            # renders: Poisson, 30 per second
+        t += rng.exponential(1 / 30.0)
+        if t >= seconds:
+            break
+        events.append((t, "render", scenes[rng.integers(0, 4)]))
+    events.sort(key=lambda e: e[0])
+    st0 = server.stats()
+    t0 = time.perf_counter()
+    ids = {}
+    kf_i = 4
+    for (te, kind, sid) in events:
+        while time.perf_counter() - t0 < te:
+            time.sleep(0.0002)
+        if kind == "kf":
+            k = kfs[kf_i % len(kfs)]
+            kf_i += 1
+            ids[server.submit_keyframe(sid, k)] = ("kf", None)
+        else:
+            W, H = res[rng.integers(0, 3)]
+            v = kfs[rng.integers(0, len(kfs))]
+            K = np.array([v.K[0] * W / v.W, v.K[1] * H / v.H, W / 2.0, H / 2.0], np.float32)
+            rid, _, _ = server.submit_render(sid, v.c2w, K, W, H)
+            ids[rid] = ("render", f"{W}x{H}")
+    done = server.wait(list(ids), timeout=600)
+    elapsed = time.perf_counter() - t0
+    st1 = server.stats()
+    server.close()
+    lat = {}
+    for rid, (kind, tag) in ids.items():
+        d = done[rid]
+        lat.setdefault(kind, []).append(d["t_done"] - d["t_submit"])
+        if tag:
+            lat.setdefault("render_" + tag, []).append(d["t_done"] - d["t_submit"])
+    pct = lambda v, q: float(np.percentile(np.array(v) * 1e3, q))
+    out = {"precision": precision, "window_s": round(elapsed, 2),
+           "mapping_rays_per_s": (st1["rays_done"] - st0["rays_done"]) / elapsed,
+           "requests": {k: len(v) for k, v in lat.items()}}
+    for k, v in lat.items():
+        out[f"{k}_ms_p50"] = pct(v, 50)
+        out[f"{k}_ms_p99"] = pct(v, 99)
+    return out
 
 
 # ----------------------------------------------------------------- our arm
@@ -362,6 +440,10 @@ def main():
             forms[prec] = {"value": n * k * world / (fms / 1e3), "ms_per_step": fms / k}
             mf.close()
 
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = {p: serving_benchmark(p, kfs, bits, args.serving_seconds) for p in (args.precision, "fp32")}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -374,6 +456,8 @@ def main():
                            "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
                 "roofline": roof, "render_mpx_s": render_mpx, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches), "forms": forms}
+        if serving:
+            line["serving"] = serving
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
