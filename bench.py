@@ -174,6 +174,60 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ----------------------------------------------------------------- quality
+
+def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, H=120, seed=0,
+                sigma_floor=0.2, ray_seed=0):
+    """Fits the room from noisy 320x240 keyframes (depth noise sigma_d >= sigma_floor
+    metres) along a smooth seeded camera path
+    (a Catmull-Rom spline through 8 interior points) for `steps` mapping steps and
+    returns PSNR (dB) and depth-L1 (m, along the ray) of held-out views of the same
+    path (every `every`-th pose, offset by half a period, never trained on) against
+    the analytic ground truth, before and after training."""
+    import numpy as np
+    import synth
+    from paper_2210_13641_gb300 import NerfMap, pack_params
+    cfg = synth.config_c2(precision=precision)
+    room = synth.make_room(seed)
+    poses = synth.room_spline_poses(room, n_poses, seed=seed + 5)
+    held = set(range(every // 2, n_poses, every))
+    train = [p for i, p in enumerate(poses) if i not in held]
+    kfs = synth.room_keyframes(room, len(train), seed=seed + 1, W=320, H=240, K=(262.5, 262.5, 160.0, 120.0),
+                               poses=train, sigma_floor=sigma_floor)
+    bits = synth.room_occupancy_bits(room, cfg.occ_res, cfg.grid_origin, cfg.grid_inv_size)
+    Kv = (525.0 * W / 640, 525.0 * H / 480, W / 2.0, H / 2.0)
+    views = synth.room_keyframes(room, len(held), seed=seed + 9, W=W, H=H, K=Kv, noise_k=0.0,
+                                 poses=[poses[i] for i in sorted(held)])
+    m = NerfMap(cfg, occ_every=0)
+    m.set_params(pack_params(synth.random_params(cfg, seed)))
+    m.set_occupancy(bits)
+    for kf in kfs:
+        m.add_keyframe(kf)
+
+    def evaluate():
+        ps, dl = [], []
+        for v in views:
+            rgb, dep, _ = m.render(v.c2w, v.K, W, H)
+            uu, vv = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+            s = np.sqrt(((uu - v.K[2]) / v.K[0]) ** 2 + ((vv - v.K[3]) / v.K[1]) ** 2 + 1.0)
+            mse = float(np.mean((rgb - v.rgb) ** 2))
+            ps.append(-10.0 * np.log10(max(mse, 1e-12)))
+            dl.append(float(np.mean(np.abs(dep - v.depth * s))))
+        return float(np.mean(ps)), float(np.mean(dl))
+
+    p0, d0 = evaluate()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        m.step(rays, seed=ray_seed, want_loss=False)
+    loss = m.step(rays, seed=ray_seed, no_update=True)
+    t = time.perf_counter() - t0
+    p1, d1 = evaluate()
+    m.close()
+    return {"precision": precision, "steps": steps, "rays_per_step": rays, "train_keyframes": len(kfs),
+            "heldout_views": len(views), "psnr_db": p1, "depth_l1_m": d1, "psnr_db_init": p0,
+            "depth_l1_m_init": d0, "final_loss": loss, "train_s": t}
+
+
 # ----------------------------------------------------------------- serving
 
 def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0):

@@ -68,7 +68,8 @@ extern "C" {
  * whose (N_l + 1)^3 vertices fit in its table is indexed densely, otherwise by the
  * spatial hash (x * 1 ^ y * 2654435761 ^ z * 805459861) mod 2^log2_table.
  * MLP widths are fixed: enc_width 32 (L * F zero padded), density_hidden 64,
- * geo_width 16, color_hidden 64.
+ * geo_width 16, color_hidden 64.  Density sigma = exp(min(h_0, 15)) (the truncated
+ * exponential of Instant-NGP), colour = sigmoid of the colour MLP's output.
  *
  * Sampling (Sec. 3.2, sampling 3D positions along the pixel's ray): step i of a
  * ray is at t_i = near_t + i * step_t, i < n_steps, grid position

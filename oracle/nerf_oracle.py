@@ -281,6 +281,12 @@ def sh_deg4(d: np.ndarray) -> np.ndarray:
 
 # ------------------------------------------------------------------ a5, a6: MLPs
 
+# Density activation: the truncated exponential of Instant-NGP (the map the paper
+# uses), sigma = exp(min(h_0, 15)).  Beyond h_0 = 15 a sample is opaque already
+# (sigma * delta > 10^4 at any spacing used here); the cap keeps sigma finite in FP32
+# and its derivative there is zero.
+SIGMA_H_MAX = 15.0
+
 def relu(a):
     return np.maximum(a, 0.0)
 
@@ -321,7 +327,7 @@ def relu_decisions(P: dict, feat: np.ndarray, sh: np.ndarray, precision: str):
 def field_forward(P: dict, feat: np.ndarray, sh: np.ndarray, decisions=None) -> dict:
     """sigma_i and c_i from one evaluation of the MLPs at the sample (Sec. 3.2: both
     are estimated simultaneously).  Density MLP: h = W2 relu(W1 feat), sigma =
-    exp(h_0).  Colour MLP on [h; SH]: c = sigmoid(W5 relu(W4 relu(W3 [h; SH]))).
+    exp(min(h_0, 15)).  Colour MLP on [h; SH]: c = sigmoid(W5 relu(W4 relu(W3 [h; SH]))).
     No biases.  `decisions` (from relu_decisions) fixes the ReLU branches; by
     default each unit is active when its FP64 pre-activation is positive.
     Returns every intermediate (for the backward pass)."""
@@ -330,7 +336,7 @@ def field_forward(P: dict, feat: np.ndarray, sh: np.ndarray, decisions=None) -> 
     m1 = a1 > 0 if decisions is None else decisions[0]
     h1 = np.where(m1, a1, 0.0)
     h = h1 @ W["W2"].T
-    sigma = np.exp(h[:, 0])
+    sigma = np.exp(np.minimum(h[:, 0], SIGMA_H_MAX))
     x3 = np.concatenate([h, sh], axis=1)
     a3 = x3 @ W["W3"].T
     m3 = a3 > 0 if decisions is None else decisions[1]
@@ -451,7 +457,7 @@ def field_backward(P: dict, fw: dict, dsigma, drgb, magnitude: bool = False):
     g["W3"] = da3.T @ fw["x3"]
     dx3 = da3 @ W["W3"]
     dh = dx3[:, :P["W2"].shape[0]].copy()
-    dh[:, 0] += dsigma * fw["sigma"]
+    dh[:, 0] += dsigma * fw["sigma"] * (fw["h"][:, 0] < SIGMA_H_MAX)
     g["W2"] = dh.T @ fw["h1"]
     dh1 = dh @ W["W2"]
     da1 = dh1 * fw["m1"]
@@ -579,7 +585,7 @@ def occupancy_refresh(cfg, P, density, refresh_idx, seed, level_res=None):
     feat, _, _ = hash_encode(cfg, level_res, P["tables"], x)
     W1 = P["W1"].astype(np.float64)
     W2 = P["W2"].astype(np.float64)
-    sig = np.exp((relu(feat @ W1.T) @ W2.T)[:, 0])
+    sig = np.exp(np.minimum((relu(feat @ W1.T) @ W2.T)[:, 0], SIGMA_H_MAX))
     newd = np.maximum(float(cfg.occ_decay) * density, sig)
     bits = np.packbits(newd > float(cfg.occ_thresh), bitorder="little")
     return newd, bits, x

@@ -22,6 +22,9 @@ constexpr int kW3 = kHid * (kGeo + kSH);  // 2048
 constexpr int kW4 = kHid * kHid;          // 4096
 constexpr int kW5 = 3 * kHid;             // 192
 constexpr int kMlpParams = kW1 + kW2 + kW3 + kW4 + kW5;  // 9408
+// Density activation: sigma = exp(min(h_0, kSigmaHMax)), the truncated exponential of
+// Instant-NGP; beyond the cap a sample is opaque already and dsigma/dh_0 = 0.
+constexpr float kSigmaHMax = 15.f;
 constexpr int kOffW1 = 0, kOffW2 = kW1, kOffW3 = kW1 + kW2, kOffW4 = kOffW3 + kW3,
               kOffW5 = kOffW4 + kW4;
 

@@ -66,7 +66,7 @@ void launch_init_params(float* p, size_t n_table, uint64_t seed, cudaStream_t s)
 
 // Occupancy refresh: one seeded point x = (c + u) / R per cell (u: three 21-bit
 // fields of one counter draw, stream kOccStream + refresh index), its density
-// sigma = exp((W2 relu(W1 enc(x)))_0) on FP32 cores, EMA d <- max(decay d, sigma),
+// sigma = exp(min((W2 relu(W1 enc(x)))_0, 15)) on FP32 cores, EMA d <- max(decay d, sigma),
 // bit = d > thresh (32 cells per ballot word).
 __global__ void __launch_bounds__(256) k_occ_refresh(DevCfg c, const float* __restrict__ params,
                                                      float* __restrict__ density,
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256) k_occ_refresh(DevCfg c, const float* __re
             for (int k = 0; k < kEnc; ++k) a += W1[j * kEnc + k] * f[k];
             h0 += W2r0[j] * fmaxf(a, 0.f);
         }
-        const float sigma = expf(h0);
+        const float sigma = expf(fminf(h0, kSigmaHMax));
         const float d = fmaxf(decay * density[cell], sigma);
         density[cell] = d;
         const uint32_t word = __ballot_sync(0xffffffffu, d > thresh);

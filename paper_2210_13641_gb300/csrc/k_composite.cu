@@ -13,8 +13,9 @@ namespace nm {
 // S_i = sum_{j>i} w_j c_j and the same with t): dL/dc_i = w_i g_I and
 // dL/dsigma_i = delta (g_I . (T_{i+1} c_i - S^c_i) + g_D (T_{i+1} t_i - S^d_i)), with
 // g_I = -2 (I - I*) / R, g_D = -2 lambda_D (D - D*) / (Sigma_D R).
-// loss[0] receives the batch loss; loss[1] the largest seed magnitude over samples
-// (FP32 bits), from which the tensor-core backward picks its gradient scale.
+// loss[0] receives the batch loss; loss[1] and loss[2] the largest density and colour
+// seed magnitudes over samples (FP32 bits), from which the tensor-core backward picks
+// its gradient scales.
 template <bool kBackward>
 __global__ void k_composite(DevCfg c, uint32_t n_rays, const float* __restrict__ rays, uint32_t cap,
                             const uint32_t* __restrict__ offsets, const float* __restrict__ ts,
@@ -22,7 +23,8 @@ __global__ void k_composite(DevCfg c, uint32_t n_rays, const float* __restrict__
                             float* __restrict__ ray_out, float* __restrict__ loss) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     float l = 0.f;
-    float gmax = 0.f;  // largest per-sample gradient seed |dL/dsigma * sigma|, |dL/dc|
+    float gmax = 0.f;  // largest per-sample density seed |dL/dsigma * sigma|
+    float cmax = 0.f;  // largest per-sample colour seed |dL/dc|
     if (r < n_rays) {
         const uint32_t a = offsets[r], b = offsets[r + 1];
         const float delta = c.step_t;
@@ -64,7 +66,8 @@ __global__ void k_composite(DevCfg c, uint32_t n_rays, const float* __restrict__
                 const float dsig = delta * (gr * (Tn * v.y - Sr) + gg * (Tn * v.z - Sg) +
                                             gb * (Tn * v.w - Sb) + gd * (Tn * t - Sd));
                 scratch[s] = make_float4(dsig, w * gr, w * gg, w * gb);
-                gmax = fmaxf(gmax, fmaxf(fabsf(dsig * v.x), fmaxf(fabsf(w * gr), fmaxf(fabsf(w * gg), fabsf(w * gb)))));
+                gmax = fmaxf(gmax, fabsf(dsig * v.x));
+                cmax = fmaxf(cmax, fmaxf(fabsf(w * gr), fmaxf(fabsf(w * gg), fabsf(w * gb))));
                 Sr += w * v.y;
                 Sg += w * v.z;
                 Sb += w * v.w;
@@ -78,11 +81,13 @@ __global__ void k_composite(DevCfg c, uint32_t n_rays, const float* __restrict__
         for (int o = 16; o > 0; o >>= 1) {
             l += __shfl_xor_sync(0xffffffffu, l, o);
             gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+            cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
         }
         if ((threadIdx.x & 31) == 0) {
             if (l != 0.f) atomicAdd(loss, l / (float)n_rays);
             // non-negative floats order like their bit patterns
             if (gmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(loss) + 1, __float_as_uint(gmax));
+            if (cmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(loss) + 2, __float_as_uint(cmax));
         }
     }
 }
@@ -91,7 +96,7 @@ void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const Ste
                       cudaStream_t s) {
     const uint32_t grid = (n_rays + 127) / 128;
     if (backward) {
-        cudaMemsetAsync(b.loss, 0, 2 * sizeof(float), s);
+        cudaMemsetAsync(b.loss, 0, 3 * sizeof(float), s);
         k_composite<true><<<grid, 128, 0, s>>>(c, n_rays, b.rays, b.cap_rays, b.offsets, b.t,
                                                b.sig_rgb, b.dsig_rgb, b.ray_out, b.loss);
     } else {

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) k_field_fwd_fp32(DevCfg c, const float* _
         float x3[32];
         density_mlp(s, f, x3);
         sh16(d.x, d.y, d.z, x3 + kGeo);
-        const float sigma = expf(x3[0]);
+        const float sigma = expf(fminf(x3[0], kSigmaHMax));
         const float3 rgb = color_mlp(s, x3);
         sig_rgb[i] = make_float4(sigma, rgb.x, rgb.y, rgb.z);
     }
@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
         const bool valid = i < n;
         float3 x = make_float3(0.f, 0.f, 0.f);
         float dsig = 0.f, sigma = 0.f;
+        bool sig_grad_off = false;
         if (valid) {
             // ---- recompute the forward pass into this sample's row
             float3 d;
@@ -233,7 +234,8 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
             sh16(d.x, d.y, d.z, x3 + kGeo);
 #pragma unroll
             for (int k = 0; k < 32; ++k) row[kRx3 + k] = x3[k];
-            sigma = expf(x3[0]);
+            sigma = expf(fminf(x3[0], kSigmaHMax));
+            if (!(x3[0] < kSigmaHMax)) sig_grad_off = true;
             float h4[kHid];
 #pragma unroll
             for (int q = 0; q < kHid; ++q) h4[q] = 0.f;
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
 #pragma unroll
                 for (int m = 0; m < kGeo; ++m) dy[m] += W3[nn * 32 + m] * a;
             }
-            dy[0] += dsig * sigma;
+            if (!sig_grad_off) dy[0] += dsig * sigma;
 #pragma unroll
             for (int m = 0; m < kGeo; ++m) row[kRx3 + m] = dy[m];
         }

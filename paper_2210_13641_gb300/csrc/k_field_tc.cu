@@ -13,9 +13,13 @@
 // products over the tile's samples (MN-major operands of the same tiles) that keep
 // accumulating in TMEM until the block has no tiles left.
 //
-// Gradient tiles are scaled by a power of two S before rounding to the MLP type:
-// S brings the step's largest per-sample gradient seed to about 2^13, which keeps
-// the small seeds out of FP16's subnormal range and leaves headroom below 65504.
+// Gradient tiles are scaled by powers of two before rounding to the MLP type: the
+// colour branch (dL/dz through the colour MLP down to its input, weights W3-W5) by
+// S_c, which brings the step's largest colour seed |dL/dc| to about 2^13, and the
+// density branch (from dL/dh on, weights W1-W2 and the tables) by S_d, which does the
+// same for the larger of the density seeds |dL/dsigma * sigma| and the colour seeds.
+// The depth term's seeds are usually far larger than the colour ones, so one shared
+// scale would push the colour gradients into FP16's subnormal range.
 // FP16 encodings enter the MLP scaled by 2^8 (table values start near 1e-4, below
 // FP16's normal range).  Both scales are exact and are removed in FP32.
 #include <cuda_bf16.h>
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(128) k_field_fwd_tc(DevCfg c, const float* __r
         }
         wait_mma(&bar, phase, timed_out);
         ld_cols<16>(trow, 0, v);
-        const float sigma = expf(v[0]);
+        const float sigma = expf(fminf(v[0], kSigmaHMax));
         if (valid) sh16(d.x, d.y, d.z, v + kGeo);
         else {
 #pragma unroll
@@ -415,9 +419,12 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
     const uint32_t n = *n_total;
     const uint32_t n_tiles = (n + 127) / 128;
     const uint32_t n_mine = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const float gm = seed_max[1];
-    const float S = gm > 0.f ? exp2f(fminf(fmaxf(floorf(log2f(8192.f / gm)), -100.f), 100.f)) : 1.f;
-    const float inv_S = 1.f / S;
+    const float gm_d = seed_max[1], gm_c = seed_max[2];
+    const float gm_dc = fmaxf(gm_d, gm_c);
+    const float S = gm_dc > 0.f ? exp2f(fminf(fmaxf(floorf(log2f(8192.f / gm_dc)), -100.f), 100.f)) : 1.f;
+    const float Sc = gm_c > 0.f ? exp2f(fminf(fmaxf(floorf(log2f(8192.f / gm_c)), -100.f), 100.f)) : S;
+    const float inv_S = 1.f / S, inv_Sc = 1.f / Sc;
+    const float c_to_d = S * inv_Sc;  // power of two: exact
     bool timed_out = false;
 
     if (warp < 4) {
@@ -449,7 +456,8 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
             wait_mma(&bar, phase, timed_out);
             float y[32];
             ld_cols<16>(trow, 0, y);
-            const float sigma = expf(y[0]);
+            const float sigma = expf(fminf(y[0], kSigmaHMax));
+            const float sig_grad = y[0] < kSigmaHMax ? sigma : 0.f;
             if (valid) sh16(rd.x, rd.y, rd.z, y + kGeo);
             else {
 #pragma unroll
@@ -504,7 +512,9 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
             }
             wait_mma(&bar, phase, timed_out);
             ld_cols<16>(trow, 0, v);
-            v[0] += S * rz.w * sigma;                                    // dL/dh_0 += dL/dsigma * sigma
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] *= c_to_d;                // colour scale -> density scale
+            v[0] += S * rz.w * sig_grad;                                 // dL/dh_0 += dL/dsigma * dsigma/dh_0
             store_row_at<BF16, 16>(tX3, r, 0, v);                        // G2 (columns 0..15)
             // dW2^T += H1^T G2 ; dH1 = G2 W2
             to_tensor_mlp();
@@ -547,11 +557,11 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
             for (int h = 0; h < 2; ++h) {
                 ld_cols<32>(trow, kColW4 + 32 * h, w);
                 if (has)
-                    for (int q = 0; q < 32; ++q) atomicAdd(gm_ + kOffW4 + m * 64 + 32 * h + q, w[q] * inv_S);
+                    for (int q = 0; q < 32; ++q) atomicAdd(gm_ + kOffW4 + m * 64 + 32 * h + q, w[q] * inv_Sc);
             }
             ld_cols<32>(trow, kColW3, w);
             if (has)
-                for (int q = 0; q < 32; ++q) atomicAdd(gm_ + kOffW3 + m * 32 + q, w[q] * inv_S);
+                for (int q = 0; q < 32; ++q) atomicAdd(gm_ + kOffW3 + m * 32 + q, w[q] * inv_Sc);
             ld_cols<32>(trow, kColW1, w);
             if (has)
                 for (int q = 0; q < 32; ++q) atomicAdd(gm_ + kOffW1 + m * 32 + q, w[q] * inv_S * inv_fs);
@@ -560,7 +570,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 for (int q = 0; q < 16; ++q) atomicAdd(gm_ + kOffW2 + q * 64 + m, w[q] * inv_S);
             ld_cols<16>(trow, kColW5T, w);
             if (has)
-                for (int q = 0; q < 3; ++q) atomicAdd(gm_ + kOffW5 + q * 64 + m, w[q] * inv_S);
+                for (int q = 0; q < 3; ++q) atomicAdd(gm_ + kOffW5 + q * 64 + m, w[q] * inv_Sc);
         }
         if (any_timeout && tid == 0) atomicOr(err, kErrTimeout);
     } else {
@@ -586,8 +596,8 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
 #pragma unroll
                 for (int q = 0; q < 4; ++q) f_next[q] = feat[(size_t)i * 4 + q];
                 rd_next = make_float4(d.x, d.y, d.z, 1.f);
-                rz_next = make_float4(S * g.y * col.y * (1.f - col.y), S * g.z * col.z * (1.f - col.z),
-                                      S * g.w * col.w * (1.f - col.w), g.x);
+                rz_next = make_float4(Sc * g.y * col.y * (1.f - col.y), Sc * g.z * col.z * (1.f - col.z),
+                                      Sc * g.w * col.w * (1.f - col.w), g.x);
             }
         };
         auto publish = [&]() {

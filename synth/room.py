@@ -145,10 +145,10 @@ def _inside_prims(room: Room, p: np.ndarray, margin: float) -> np.ndarray:
 
 def room_keyframes(room: Room, n: int, seed: int = 0, W: int = 640, H: int = 480,
                    K=(525.0, 525.0, 320.0, 240.0), noise_k: float = 0.01,
-                   poses=None, first_id: int = 0):
+                   poses=None, first_id: int = 0, sigma_floor: float = 0.0):
     """`n` keyframes at seeded poses inside the room looking at random interior
-    points.  depth = z + N(0, sigma_d^2), sigma_d = noise_k * z^2 * U[0.5, 2],
-    var = sigma_d^2 (z-depth units)."""
+    points.  depth = z + N(0, sigma_d^2), sigma_d = max(noise_k * z^2 * U[0.5, 2],
+    sigma_floor), var = sigma_d^2 (z-depth units)."""
     rng = np.random.default_rng(seed)
     K = np.asarray(K, np.float32)
     E = room.extent
@@ -167,7 +167,7 @@ def room_keyframes(room: Room, n: int, seed: int = 0, W: int = 640, H: int = 480
                     break
             c2w = look_at_pose(eye, tgt)
         z, rgb = render_room(room, c2w, K, W, H)
-        sigma = noise_k * z * z * rng.uniform(0.5, 2.0, size=z.shape)
+        sigma = np.maximum(noise_k * z * z * rng.uniform(0.5, 2.0, size=z.shape), sigma_floor)
         depth = z + rng.normal(size=z.shape) * sigma
         out.append(Keyframe(first_id + k, c2w.astype(np.float32), K, W, H,
                             rgb.astype(np.float32), depth.astype(np.float32),
@@ -195,33 +195,41 @@ def room_occupancy_bits(room: Room, res: int, grid_origin, grid_inv_size) -> np.
     return np.packbits(bits, bitorder="little")
 
 
-def room_spline_poses(room: Room, n: int, seed: int = 0, n_ctrl: int = 8):
+def room_spline_poses(room: Room, n: int, seed: int = 0, n_ctrl: int = 8, clearance: float = 0.3):
     """`n` poses along a Catmull-Rom spline through `n_ctrl` seeded control points,
-    each looking at a point further along the path."""
+    each looking at a point further along the path.  Control points are redrawn
+    until every camera centre on the path keeps `clearance` from the walls and from
+    every primitive."""
     rng = np.random.default_rng(seed)
     E = room.extent
-    ctrl = []
-    while len(ctrl) < n_ctrl:
-        p = rng.uniform(0.6, E - 0.6)
-        if not _inside_prims(room, p[None], 0.2)[0]:
-            ctrl.append(p)
-    ctrl = np.array(ctrl)
-    P = np.concatenate([ctrl[:1], ctrl, ctrl[-1:]], 0)
+    for _ in range(1000):
+        ctrl = []
+        while len(ctrl) < n_ctrl:
+            p = rng.uniform(0.6, E - 0.6)
+            if not _inside_prims(room, p[None], clearance)[0]:
+                ctrl.append(p)
+        ctrl = np.array(ctrl)
+        P = np.concatenate([ctrl[:1], ctrl, ctrl[-1:]], 0)
 
-    def cr(s):
-        s = np.clip(s, 0, n_ctrl - 1 - 1e-9)
-        i = int(s)
-        u = s - i
-        p0, p1, p2, p3 = P[i], P[i + 1], P[i + 2], P[i + 3]
-        return 0.5 * ((2 * p1) + (-p0 + p2) * u + (2 * p0 - 5 * p1 + 4 * p2 - p3) * u * u
-                      + (-p0 + 3 * p1 - 3 * p2 + p3) * u ** 3)
+        def cr(s):
+            s = np.clip(s, 0, n_ctrl - 1 - 1e-9)
+            i = int(s)
+            u = s - i
+            p0, p1, p2, p3 = P[i], P[i + 1], P[i + 2], P[i + 3]
+            return 0.5 * ((2 * p1) + (-p0 + p2) * u + (2 * p0 - 5 * p1 + 4 * p2 - p3) * u * u
+                          + (-p0 + 3 * p1 - 3 * p2 + p3) * u ** 3)
 
+        eyes = np.array([cr(k * (n_ctrl - 1) / max(n - 1, 1)) for k in range(n)])
+        clear = (np.all((eyes > clearance) & (eyes < E - clearance))
+                 and not np.any(_inside_prims(room, eyes, clearance)))
+        if clear:
+            break
     poses = []
     for k in range(n):
         s = k * (n_ctrl - 1) / max(n - 1, 1)
-        eye = cr(s)
-        tgt = cr(min(s + 0.5, n_ctrl - 1)) + np.array([0.0, 0.0, -0.3])
-        if np.linalg.norm(tgt - eye) < 0.3:
-            tgt = eye + np.array([1.0, 0.3, -0.2])
+        eye = eyes[k]
+        tgt = cr(min(s + 0.5, n_ctrl - 1)) + np.array([0.0, 0.0, -0.1])
+        if np.linalg.norm(tgt - eye) < 0.5:
+            tgt = eye + np.array([1.0, 0.3, -0.1])
         poses.append(look_at_pose(eye, tgt))
     return poses

@@ -495,3 +495,22 @@ def test_operand_rounding_and_relu_decisions():
         flip1 = m1 != (fw["a1"] > 0)
         assert np.all(np.abs(fw["a1"][flip1]) <= 8 * u * mag1[flip1])
         assert (m3 != (fw["a3"] > 0)).mean() < 0.05 and (m4 != (fw["a4"] > 0)).mean() < 0.05
+
+
+def test_density_cap_is_opaque_and_flat():
+    """sigma = exp(min(h_0, 15)): above the cap the value is exp(15) and the loss
+    does not depend on h_0 (zero derivative, checked by central differences)."""
+    P = {"W1": np.zeros((64, 32)), "W2": np.zeros((16, 64)), "W3": np.zeros((64, 32)),
+         "W4": np.zeros((64, 64)), "W5": np.zeros((3, 64))}
+    P["W1"][0, 0] = 1.0
+    P["W2"][0, 0] = 20.0                                 # h_0 = 20 * relu(f_0)
+    f = np.zeros((1, 32)); f[0, 0] = 1.0
+    sh = np.zeros((1, 16))
+    fw = oracle.field_forward(P, f, sh)
+    assert fw["sigma"][0] == pytest.approx(math.exp(15.0), rel=1e-15)
+    g, _ = oracle.field_backward(P, fw, np.array([1.0]), np.zeros((1, 3)))
+    assert g["W2"][0, 0] == 0.0 and g["W1"][0, 0] == 0.0
+    P["W2"][0, 0] = 10.0                                 # below the cap: d sigma / d h_0 = sigma
+    fw = oracle.field_forward(P, f, sh)
+    g, _ = oracle.field_backward(P, fw, np.array([1.0]), np.zeros((1, 3)))
+    assert g["W2"][0, 0] == pytest.approx(math.exp(10.0), rel=1e-12)
