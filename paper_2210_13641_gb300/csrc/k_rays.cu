@@ -122,32 +122,41 @@ void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t 
 }
 
 // ---------------------------------------------------------------- march
-// Pass 1 counts the retained steps of each ray, pass 2 (after the scan) writes
-// (ray, t) of each retained step at the ray's offset, in step order.
-template <bool kEmit>
+// One pass over the steps of each ray: the t of every retained step goes to the
+// ray's slot row (max_samples floats per ray, in step order) and the count to
+// counts[r].  After the scan, k_compact copies each ray's row to its offset (one
+// warp per ray, coalesced) and writes the ray index beside each sample.
 __global__ void k_march(DevCfg c, const uint32_t* __restrict__ bits, uint32_t n_rays,
                         const float* __restrict__ rays, uint32_t cap, uint32_t* __restrict__ counts,
-                        const uint32_t* __restrict__ offsets, uint32_t* __restrict__ ray_id,
-                        float* __restrict__ ts) {
+                        float* __restrict__ slots) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
     const float3 o = make_float3(rays[kOx * cap + r], rays[kOy * cap + r], rays[kOz * cap + r]);
     const float3 d = make_float3(rays[kDx * cap + r], rays[kDy * cap + r], rays[kDz * cap + r]);
     uint32_t n = 0;
-    const uint32_t base = kEmit ? offsets[r] : 0;
+    float* row = slots + (size_t)r * c.max_samples;
     uint32_t i_lo, i_hi;
     box_step_range(c, o, d, i_lo, i_hi);
     for (uint32_t i = i_lo; i < i_hi && n < c.max_samples; ++i) {
         const float t = sample_t(c, i);
         const float3 x = grid_pos(c, o, d, t);
         if (!in_box(c, x) || !occupied(c, bits, x)) continue;
-        if (kEmit) {
-            ray_id[base + n] = r;
-            ts[base + n] = t;
-        }
-        ++n;
+        row[n++] = t;
     }
-    if (!kEmit) counts[r] = n;
+    counts[r] = n;
+}
+
+__global__ void k_compact(uint32_t n_rays, uint32_t max_samples, const uint32_t* __restrict__ offsets,
+                          const float* __restrict__ slots, uint32_t* __restrict__ ray_id, float* __restrict__ ts) {
+    const uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (r >= n_rays) return;
+    const uint32_t a = offsets[r], n = offsets[r + 1] - a;
+    const float* row = slots + (size_t)r * max_samples;
+    for (uint32_t k = lane; k < n; k += 32) {
+        ts[a + k] = row[k];
+        ray_id[a + k] = r;
+    }
 }
 
 // Exclusive scan of counts[0..n) into offsets[0..n], offsets[n] = total.
@@ -236,15 +245,14 @@ __global__ void k_scan_add(uint32_t* __restrict__ out, uint32_t n,
 
 void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, const StepBufs& b,
                   cudaStream_t s) {
-    const uint32_t grid = (n_rays + 127) / 128;
-    k_march<false><<<grid, 128, 0, s>>>(c, occ_bits, n_rays, b.rays, b.cap_rays, b.counts,
-                                        nullptr, nullptr, nullptr);
+    // slot rows live in the (not yet used) per-sample colour buffer: cap_samples floats
+    float* slots = reinterpret_cast<float*>(b.sig_rgb);
+    k_march<<<(n_rays + 127) / 128, 128, 0, s>>>(c, occ_bits, n_rays, b.rays, b.cap_rays, b.counts, slots);
     const uint32_t n_tiles = (n_rays + kScanTile - 1) / kScanTile;  // <= kScanTile (n <= 2^24)
     k_scan_tiles<<<n_tiles, kScanThreads, 0, s>>>(b.counts, n_rays, b.offsets, b.block_sums);
     k_scan_top<<<1, kScanThreads, 0, s>>>(b.block_sums, n_tiles, b.offsets + n_rays);
     k_scan_add<<<(n_rays + 255) / 256, 256, 0, s>>>(b.offsets, n_rays, b.block_sums);
-    k_march<true><<<grid, 128, 0, s>>>(c, occ_bits, n_rays, b.rays, b.cap_rays, nullptr,
-                                       b.offsets, b.ray_id, b.t);
+    k_compact<<<(n_rays + 7) / 8, 256, 0, s>>>(n_rays, c.max_samples, b.offsets, slots, b.ray_id, b.t);
 }
 
 }  // namespace nm
