@@ -13,54 +13,82 @@ __device__ __forceinline__ float corner_weight(int k, float wx, float wy, float 
     return ((k & 1) ? wx : 1.f - wx) * ((k & 2) ? wy : 1.f - wy) * ((k & 4) ? wz : 1.f - wz);
 }
 
-// Encodes grid position x into f[0 .. 2L) (f[2L .. 32) set to zero).
-// tables: [L][T] float2.  Levels are processed in groups of kGatherGroup: the
-// group's 8 * kGatherGroup slots are computed first and all its loads issued
-// before any is used, so that many table reads are in flight per thread.
+// Corners k and k + 1 (k even) differ only in x.  Their slots s and s' share one
+// aligned 16-byte chunk (two float2 entries) exactly when s' = s ^ 1: in a hashed
+// level that holds whenever cx is even (the x coordinate enters the hash by xor with
+// prime 1), in a dense level whenever s is even.  The encoding reads such a pair
+// with one 16-byte load.  (The gradient scatter keeps one 8-byte reduction per
+// corner: 16-byte reductions of the shared pairs made the backward slower.)
+__device__ __forceinline__ bool x_pair_shared(uint32_t s0, uint32_t s1) { return (s0 ^ s1) == 1u; }
+
+// Features of levels l0 .. l0 + kGatherGroup - 1 of grid position x into
+// f[0 .. 2 kGatherGroup) (zero for levels >= L).  tables: [L][T] float2.  The
+// group's slots are computed first and all its loads issued before any is used,
+// so that many table reads are in flight per thread.  An x-pair of corners in one
+// chunk is read with one 16-byte load (halves swapped when corner k is the upper
+// one), any other pair with two 8-byte loads.
 constexpr int kGatherGroup = 4;
 
-__device__ __forceinline__ void hash_encode(const DevCfg& c, const float2* __restrict__ tables,
-                                            float3 x, float* f) {
+__device__ __forceinline__ void encode_group(const DevCfg& c, const float2* __restrict__ tables, float3 x,
+                                             int l0, float* f) {
     const uint32_t Tmask = c.T - 1;
+    float4 q[kGatherGroup][4];   // (corner 2j, corner 2j + 1), halves swapped if bit j of swp
+    uint32_t swp[kGatherGroup];
+    float w[kGatherGroup][3];
 #pragma unroll
-    for (int l0 = 0; l0 < kEnc / 2; l0 += kGatherGroup) {
-        float2 v[kGatherGroup][8];
-        float w[kGatherGroup][3];
+    for (int g = 0; g < kGatherGroup; ++g) {
+        const int l = l0 + g;
+        swp[g] = 0u;
+        if (l < (int)c.L) {
+            const uint32_t N = c.res[l];
+            const bool dense = (c.dense_mask >> l) & 1u;
+            uint32_t cx, cy, cz;
+            level_cell(x.x, N, cx, w[g][0]);
+            level_cell(x.y, N, cy, w[g][1]);
+            level_cell(x.z, N, cz, w[g][2]);
+            const float2* tab = tables + (size_t)l * c.T;
 #pragma unroll
-        for (int g = 0; g < kGatherGroup; ++g) {
-            const int l = l0 + g;
-            if (l < (int)c.L) {
-                const uint32_t N = c.res[l];
-                const bool dense = (c.dense_mask >> l) & 1u;
-                uint32_t cx, cy, cz;
-                level_cell(x.x, N, cx, w[g][0]);
-                level_cell(x.y, N, cy, w[g][1]);
-                level_cell(x.z, N, cz, w[g][2]);
-                const float2* tab = tables + (size_t)l * c.T;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t slot = vertex_slot(cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1),
-                                                      N, dense, Tmask);
-                    v[g][k] = __ldg(tab + slot);
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t yy = cy + (j & 1), zz = cz + (j >> 1);
+                const uint32_t s0 = vertex_slot(cx, yy, zz, N, dense, Tmask);
+                const uint32_t s1 = vertex_slot(cx + 1, yy, zz, N, dense, Tmask);
+                if (x_pair_shared(s0, s1)) {
+                    q[g][j] = __ldg(reinterpret_cast<const float4*>(tab + (s0 & ~1u)));
+                    swp[g] |= (s0 & 1u) << j;
+                } else {
+                    const float2 a = __ldg(tab + s0), b = __ldg(tab + s1);
+                    q[g][j] = make_float4(a.x, a.y, b.x, b.y);
                 }
             }
-        }
-#pragma unroll
-        for (int g = 0; g < kGatherGroup; ++g) {
-            const int l = l0 + g;
-            float a0 = 0.f, a1 = 0.f;
-            if (l < (int)c.L) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const float wk = corner_weight(k, w[g][0], w[g][1], w[g][2]);
-                    a0 += wk * v[g][k].x;
-                    a1 += wk * v[g][k].y;
-                }
-            }
-            f[2 * l] = a0;
-            f[2 * l + 1] = a1;
         }
     }
+#pragma unroll
+    for (int g = 0; g < kGatherGroup; ++g) {
+        const int l = l0 + g;
+        float a0 = 0.f, a1 = 0.f;
+        if (l < (int)c.L) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool hi = (swp[g] >> j) & 1u;
+                const float4 v = q[g][j];
+                const float w0 = corner_weight(2 * j, w[g][0], w[g][1], w[g][2]);
+                const float w1 = corner_weight(2 * j + 1, w[g][0], w[g][1], w[g][2]);
+                a0 += w0 * (hi ? v.z : v.x);
+                a1 += w0 * (hi ? v.w : v.y);
+                a0 += w1 * (hi ? v.x : v.z);
+                a1 += w1 * (hi ? v.y : v.w);
+            }
+        }
+        f[2 * g] = a0;
+        f[2 * g + 1] = a1;
+    }
+}
+
+// Encodes grid position x into f[0 .. 2L) (f[2L .. 32) set to zero).
+__device__ __forceinline__ void hash_encode(const DevCfg& c, const float2* __restrict__ tables,
+                                            float3 x, float* f) {
+#pragma unroll
+    for (int l0 = 0; l0 < kEnc / 2; l0 += kGatherGroup) encode_group(c, tables, x, l0, f + 2 * l0);
 }
 
 // dL/dtable[l][slot_k] += w_k * dL/df_l for every corner and level (FP32 atomics,
@@ -97,11 +125,13 @@ __device__ __forceinline__ void hash_scatter(const DevCfg& c, float2* __restrict
 // consecutive lanes) first sum their 8 corner contributions with a segmented
 // shuffle reduction, and only the first lane of each run issues the 8 atomics.
 // A level whose 32 cells are all different skips the reduction.
+// The level loop is not unrolled: the unrolled form's code did not fit the
+// instruction cache next to the tensor-core layer chain of the backward kernel.
 __device__ __forceinline__ void hash_scatter_warp(const DevCfg& c, float2* __restrict__ gtables,
                                                   float3 x, const float* df, bool valid) {
     const uint32_t Tmask = c.T - 1;
     const uint32_t lane = threadIdx.x & 31u;
-#pragma unroll
+#pragma unroll 1
     for (int l = 0; l < kEnc / 2; ++l) {
         if (l >= (int)c.L) break;
         const uint32_t N = c.res[l];

@@ -15,11 +15,14 @@
 //
 // Gradient tiles are scaled by powers of two before rounding to the MLP type: the
 // colour branch (dL/dz through the colour MLP down to its input, weights W3-W5) by
-// S_c, which brings the step's largest colour seed |dL/dc| to about 2^13, and the
+// S_c, which brings the step's largest colour seed |dL/dc| to about 2^8, and the
 // density branch (from dL/dh on, weights W1-W2 and the tables) by S_d, which does the
 // same for the larger of the density seeds |dL/dsigma * sigma| and the colour seeds.
 // The depth term's seeds are usually far larger than the colour ones, so one shared
-// scale would push the colour gradients into FP16's subnormal range.
+// scale would push the colour gradients into FP16's subnormal range.  2^8 leaves a
+// factor 2^8 of headroom below FP16's largest value for the growth of the gradient
+// through the layers (fan-in 64) and keeps seeds down to 2^-22 of the largest one
+// normal; with 2^13 the deepest colour-branch tiles saturated in trained fields.
 // FP16 encodings enter the MLP scaled by 2^8 (table values start near 1e-4, below
 // FP16's normal range).  Both scales are exact and are removed in FP32.
 #include <cuda_bf16.h>
@@ -36,18 +39,23 @@ using namespace tc;
 namespace {
 
 constexpr uint32_t kWaitPolls = 1u << 24;
+constexpr float kGradTarget = 256.f;  // largest scaled gradient seed (see above)
 
-template <bool BF16>
+// Two values rounded to the MLP type, a in the low half: one cvt to a packed pair
+// (the pair's first source operand fills the upper half).  FP16 saturates at the
+// largest finite value (+-65504) instead of overflowing; RELU also maps negative
+// values to zero.
+template <bool BF16, bool RELU = false>
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
+    uint32_t d;
     if constexpr (BF16) {
-        __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<uint32_t*>(&v);
+        if constexpr (RELU) asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+        else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
     } else {
-        a = fminf(fmaxf(a, -65504.f), 65504.f);
-        b = fminf(fmaxf(b, -65504.f), 65504.f);
-        __half2 v = __floats2half2_rn(a, b);
-        return *reinterpret_cast<uint32_t*>(&v);
+        if constexpr (RELU) asm("cvt.rn.relu.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+        else asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
     }
+    return d;
 }
 
 template <bool BF16>
@@ -70,6 +78,21 @@ __device__ __forceinline__ void store_row(uint8_t* tile, int r, const float* v) 
         q.z = pack2<BF16>(v[8 * g + 4], v[8 * g + 5]);
         q.w = pack2<BF16>(v[8 * g + 6], v[8 * g + 7]);
         *reinterpret_cast<uint4*>(tile + tile_offset(r, 8 * g, 128)) = q;
+    }
+}
+
+// C columns of row r of a 128-row tile from C floats, starting at column c0
+// (RELU: max(v, 0) is stored).
+template <bool BF16, int C, bool RELU = false>
+__device__ __forceinline__ void store_row_at(uint8_t* tile, int r, int c0, const float* v) {
+#pragma unroll
+    for (int g = 0; g < C / 8; ++g) {
+        uint4 q;
+        q.x = pack2<BF16, RELU>(v[8 * g + 0], v[8 * g + 1]);
+        q.y = pack2<BF16, RELU>(v[8 * g + 2], v[8 * g + 3]);
+        q.z = pack2<BF16, RELU>(v[8 * g + 4], v[8 * g + 5]);
+        q.w = pack2<BF16, RELU>(v[8 * g + 6], v[8 * g + 7]);
+        *reinterpret_cast<uint4*>(tile + tile_offset(r, c0 + 8 * g, 128)) = q;
     }
 }
 
@@ -158,11 +181,11 @@ constexpr int kT32 = 128 * 32 * 2, kT64 = 128 * 64 * 2, kT16 = 128 * 16 * 2;
 
 }  // namespace
 
-constexpr int kFwdSmem = kWB + kT32 + kT64 + kT64;                     // 61440
+constexpr int kFwdSmem = kWB + kT32 + kT64;                            // 45056
 
 // ------------------------------------------------------------------ forward
 template <bool BF16>
-__global__ void __launch_bounds__(128) k_field_fwd_tc(DevCfg c, const float* __restrict__ params,
+__global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* __restrict__ params,
                                                       const float* __restrict__ rays, uint32_t cap,
                                                       const uint32_t* __restrict__ n_total,
                                                       const uint32_t* __restrict__ ray_id,
@@ -178,8 +201,8 @@ __global__ void __launch_bounds__(128) k_field_fwd_tc(DevCfg c, const float* __r
     uint8_t* sW4 = sW3 + kW3B;
     uint8_t* sW5 = sW4 + kW4B;
     uint8_t* tA = smem + kWB;   // X0, X3   (128 x 32)
-    uint8_t* tB = tA + kT32;    // H1, H3   (128 x 64)
-    uint8_t* tC = tB + kT64;    // H4       (128 x 64)
+    uint8_t* tB = tA + kT32;    // H1, H3, H4 (128 x 64): a layer's MMAs have completed
+                                // before its output overwrites its input
 
     const int tid = threadIdx.x, warp = tid >> 5;
     load_weight_tiles<BF16>(params + (size_t)c.L * c.T * 2, sW1, sW2, sW3, sW4, sW5);
@@ -201,22 +224,28 @@ __global__ void __launch_bounds__(128) k_field_fwd_tc(DevCfg c, const float* __r
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t i = tile * 128 + tid;
         const bool valid = i < n;
-        float v[64];
+        float v[32];
         float3 d = make_float3(0.f, 0.f, 0.f);
-        if (valid) {
-            const float3 x = sample_pos_tc(c, rays, cap, ray_id[i], ts[i], d);
-            hash_encode(c, tables, x, v);
+        float3 x = make_float3(0.f, 0.f, 0.f);
+        if (valid) x = sample_pos_tc(c, rays, cap, ray_id[i], ts[i], d);
+        // one group of kGatherGroup = 4 levels = 8 features = one 16-byte chunk of the row
+#pragma unroll 1
+        for (int g = 0; g < kEnc / 8; ++g) {
+            if (valid) {
+                encode_group(c, tables, x, kGatherGroup * g, v);
 #pragma unroll
-            for (int k = 0; k < kEnc; ++k) v[k] *= feat_scale;
-        } else {
+                for (int k = 0; k < 8; ++k) v[k] *= feat_scale;
+            } else {
 #pragma unroll
-            for (int k = 0; k < kEnc; ++k) v[k] = 0.f;
-        }
-        store_row<BF16, 32>(tA, tid, v);
-        if (feat_out && valid) {
-#pragma unroll
-            for (int g = 0; g < 4; ++g)
-                feat_out[(size_t)i * 4 + g] = *reinterpret_cast<const uint4*>(tA + tile_offset(tid, 8 * g, 128));
+                for (int k = 0; k < 8; ++k) v[k] = 0.f;
+            }
+            uint4 q;
+            q.x = pack2<BF16>(v[0], v[1]);
+            q.y = pack2<BF16>(v[2], v[3]);
+            q.z = pack2<BF16>(v[4], v[5]);
+            q.w = pack2<BF16>(v[6], v[7]);
+            *reinterpret_cast<uint4*>(tA + tile_offset(tid, 8 * g, 128)) = q;
+            if (feat_out && valid) feat_out[(size_t)i * 4 + g] = q;
         }
         // layer 1: D = X0 W1^T (128 x 64)
         to_tensor();
@@ -225,10 +254,13 @@ __global__ void __launch_bounds__(128) k_field_fwd_tc(DevCfg c, const float* __r
             mma_commit(&bar);
         }
         wait_mma(&bar, phase, timed_out);
-        ld_cols<64>(trow, 0, v);
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = fmaxf(v[k] * inv_fs, 0.f);
-        store_row<BF16, 64>(tB, tid, v);
+        for (int h = 0; h < 64; h += 32) {  // 32-column halves keep fewer values live
+            ld_cols<32>(trow, h, v);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) v[k] *= inv_fs;
+            store_row_at<BF16, 32, true>(tB, tid, h, v);
+        }
         // layer 2: y = H1 W2^T (128 x 16)
         to_tensor();
         if (tid == 0) {
@@ -251,10 +283,11 @@ __global__ void __launch_bounds__(128) k_field_fwd_tc(DevCfg c, const float* __r
             mma_commit(&bar);
         }
         wait_mma(&bar, phase, timed_out);
-        ld_cols<64>(trow, 0, v);
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = fmaxf(v[k], 0.f);
-        store_row<BF16, 64>(tB, tid, v);
+        for (int h = 0; h < 64; h += 32) {
+            ld_cols<32>(trow, h, v);
+            store_row_at<BF16, 32, true>(tB, tid, h, v);
+        }
         // layer 4: H4 = relu(H3 W4^T)
         to_tensor();
         if (tid == 0) {
@@ -262,14 +295,15 @@ __global__ void __launch_bounds__(128) k_field_fwd_tc(DevCfg c, const float* __r
             mma_commit(&bar);
         }
         wait_mma(&bar, phase, timed_out);
-        ld_cols<64>(trow, 0, v);
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = fmaxf(v[k], 0.f);
-        store_row<BF16, 64>(tC, tid, v);
+        for (int h = 0; h < 64; h += 32) {
+            ld_cols<32>(trow, h, v);
+            store_row_at<BF16, 32, true>(tB, tid, h, v);
+        }
         // layer 5: z = H4 W5^T (3 of 16 columns used)
         to_tensor();
         if (tid == 0) {
-            gemm(tmem, kmaj(tC, 128), kmaj(sW5, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
+            gemm(tmem, kmaj(tB, 128), kmaj(sW5, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
             mma_commit(&bar);
         }
         wait_mma(&bar, phase, timed_out);
@@ -326,20 +360,6 @@ __device__ __forceinline__ void to_tensor_mlp() {
     fence_after_sync();
 }
 
-// C columns of row r of a 128-row tile from C floats, starting at column c0.
-template <bool BF16, int C>
-__device__ __forceinline__ void store_row_at(uint8_t* tile, int r, int c0, const float* v) {
-#pragma unroll
-    for (int g = 0; g < C / 8; ++g) {
-        uint4 q;
-        q.x = pack2<BF16>(v[8 * g + 0], v[8 * g + 1]);
-        q.y = pack2<BF16>(v[8 * g + 2], v[8 * g + 3]);
-        q.z = pack2<BF16>(v[8 * g + 4], v[8 * g + 5]);
-        q.w = pack2<BF16>(v[8 * g + 6], v[8 * g + 7]);
-        *reinterpret_cast<uint4*>(tile + tile_offset(r, c0 + 8 * g, 128)) = q;
-    }
-}
-
 // 64 accumulator columns -> relu(scale * a) into a 64-column tile; the ReLU branch
 // of each column is returned as two 32-bit masks.
 template <bool BF16>
@@ -352,11 +372,10 @@ __device__ __forceinline__ void relu_epilogue(uint32_t trow, uint8_t* tile, int 
         uint32_t m = 0;
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-            const float a = v[k] * scale;
-            if (a > 0.f) m |= 1u << k;
-            v[k] = fmaxf(a, 0.f);
+            v[k] *= scale;
+            if (v[k] > 0.f) m |= 1u << k;
         }
-        store_row_at<BF16, 32>(tile, r, 32 * h, v);
+        store_row_at<BF16, 32, true>(tile, r, 32 * h, v);
         if (h == 0) ma = m;
         else mb = m;
     }
@@ -421,8 +440,8 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
     const uint32_t n_mine = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const float gm_d = seed_max[1], gm_c = seed_max[2];
     const float gm_dc = fmaxf(gm_d, gm_c);
-    const float S = gm_dc > 0.f ? exp2f(fminf(fmaxf(floorf(log2f(8192.f / gm_dc)), -100.f), 100.f)) : 1.f;
-    const float Sc = gm_c > 0.f ? exp2f(fminf(fmaxf(floorf(log2f(8192.f / gm_c)), -100.f), 100.f)) : S;
+    const float S = gm_dc > 0.f ? exp2f(fminf(fmaxf(floorf(log2f(kGradTarget / gm_dc)), -100.f), 100.f)) : 1.f;
+    const float Sc = gm_c > 0.f ? exp2f(fminf(fmaxf(floorf(log2f(kGradTarget / gm_c)), -100.f), 100.f)) : S;
     const float inv_S = 1.f / S, inv_Sc = 1.f / Sc;
     const float c_to_d = S * inv_Sc;  // power of two: exact
     bool timed_out = false;
@@ -651,7 +670,7 @@ static void fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const 
         attr = true;
     }
     const float fs = BF16 ? 1.f : 256.f;
-    k_field_fwd_tc<BF16><<<n_sm * 3, 128, kFwdSmem, s>>>(c, params, b.rays, b.cap_rays, b.offsets + n_rays,
+    k_field_fwd_tc<BF16><<<n_sm * 4, 128, kFwdSmem, s>>>(c, params, b.rays, b.cap_rays, b.offsets + n_rays,
                                                           b.ray_id, b.t, b.sig_rgb,
                                                           store_feat ? reinterpret_cast<uint4*>(b.feat) : nullptr,
                                                           fs, b.err);

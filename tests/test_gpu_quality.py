@@ -2,12 +2,15 @@
 path raises the PSNR and lowers the depth error of held-out analytic views of the
 path, and the FP16 tensor-core form reaches the quality of the plain FP32 form.
 
-"Reaches" is measured against the plain form's own spread: two FP32 runs that differ
-only in the seed of the ray draws end some tenths of a dB apart, so the FP16 run
-(same seeds as the first FP32 run) must land within max(0.1 dB, twice that spread)
-in PSNR and within max(1 %, twice the spread) in depth-L1 after 3000 steps; and it
-must get there in at most 35 % of the FP32 training time.  The measured numbers are
-appended to NERFMAP_QUALITY_REPORT (JSON lines) when that is set."""
+One 3000-step fit ends with a held-out PSNR that scatters by about 0.25 dB (standard
+deviation) between ray seeds, and by about as much between two runs with the same
+seed (the table gradients are summed by atomics in varying order), and a depth-L1
+that scatters by about 1.2 %.  So each form is fitted with three ray seeds and the
+means are compared: the FP16 mean may fall short of the FP32 mean by at most 0.5 dB
+in PSNR and 3 % in depth-L1 (twice the scatter of a difference of two 3-run means;
+ending better is no failure), the BF16 mean (8 significand bits) by at most 1 dB and
+5 %.  The FP16 form must also train in at most 35 % of the FP32 time.  The measured
+numbers are appended to NERFMAP_QUALITY_REPORT (JSON lines) when that is set."""
 
 import json
 import os
@@ -15,6 +18,12 @@ import os
 import pytest
 
 pytestmark = pytest.mark.gpu
+
+SEEDS = (0, 1, 2)
+
+
+def _mean(rs, key):
+    return sum(r[key] for r in rs) / len(rs)
 
 
 def test_fp16_fit_matches_fp32_quality():
@@ -24,20 +33,19 @@ def test_fp16_fit_matches_fp32_quality():
     __graft_entry__.build()
     torch.cuda.set_device(0)
     steps = 3000
-    r32 = bench.quality_run("fp32", steps=steps)
-    r32b = bench.quality_run("fp32", steps=steps, ray_seed=1)
-    r16 = bench.quality_run("fp16", steps=steps)
-    rbf = bench.quality_run("bf16", steps=steps)
+    runs = {p: [bench.quality_run(p, steps=steps, ray_seed=s) for s in SEEDS] for p in ("fp32", "fp16", "bf16")}
     path = os.environ.get("NERFMAP_QUALITY_REPORT")
     if path:
         with open(path, "a") as f:
-            for r, tag in ((r32, "fp32"), (r32b, "fp32_ray_seed_1"), (r16, "fp16"), (rbf, "bf16")):
-                f.write(json.dumps({"run": tag, **r}) + "\n")
-    for r in (r32, r32b, r16, rbf):
-        assert r["psnr_db"] > r["psnr_db_init"] + 8.0
-        assert r["depth_l1_m"] < 0.5 * r["depth_l1_m_init"]
-    psnr_spread = abs(r32b["psnr_db"] - r32["psnr_db"])
-    depth_spread = abs(r32b["depth_l1_m"] - r32["depth_l1_m"]) / r32["depth_l1_m"]
-    assert abs(r16["psnr_db"] - r32["psnr_db"]) <= max(0.1, 2 * psnr_spread)
-    assert abs(r16["depth_l1_m"] - r32["depth_l1_m"]) / r32["depth_l1_m"] <= max(0.01, 2 * depth_spread)
-    assert r16["train_s"] <= 0.35 * r32["train_s"]
+            for p, rs in runs.items():
+                for s, r in zip(SEEDS, rs):
+                    f.write(json.dumps({"run": p, "ray_seed": s, **r}) + "\n")
+    for rs in runs.values():
+        for r in rs:
+            assert r["psnr_db"] > r["psnr_db_init"] + 8.0
+            assert r["depth_l1_m"] < 0.5 * r["depth_l1_m_init"]
+    p32, d32 = _mean(runs["fp32"], "psnr_db"), _mean(runs["fp32"], "depth_l1_m")
+    for prec, dp, dd in (("fp16", 0.5, 0.03), ("bf16", 1.0, 0.05)):
+        assert p32 - _mean(runs[prec], "psnr_db") <= dp, prec
+        assert (_mean(runs[prec], "depth_l1_m") - d32) / d32 <= dd, prec
+    assert _mean(runs["fp16"], "train_s") <= 0.35 * _mean(runs["fp32"], "train_s")
