@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"])
     p.add_argument("--no-forms", action="store_true", help="skip timing the other MLP precisions")
     p.add_argument("--no-serving", action="store_true", help="skip the multi-scene serving measurement")
+    p.add_argument("--no-large-map", action="store_true", help="skip the large-map precision comparison")
+    p.add_argument("--large-map-keyframes", type=int, default=2000)
     p.add_argument("--serving-seconds", type=float, default=6.0)
     p.add_argument("--rays", type=int, default=N_RAYS)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -226,6 +228,62 @@ def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, 
     return {"precision": precision, "steps": steps, "rays_per_step": rays, "train_keyframes": len(kfs),
             "heldout_views": len(views), "psnr_db": p1, "depth_l1_m": d1, "psnr_db_init": p0,
             "depth_l1_m_init": d0, "final_loss": loss, "train_s": t}
+
+
+# ----------------------------------------------------------------- large map
+
+def large_map_benchmark(n_kf=2000, W=1200, H=680, rays=1 << 20, steps=5, warmup=2, seed=0):
+    """The large-map configuration: L=16, T=2^22, N 16..8192, 256^3 occupancy over a
+    20x20x3 m multi-room floor (16 rooms, doorways, 128 primitives), `n_kf` keyframes
+    of W x H rendered on the GPU, `rays` rays per step.  Each MLP form (BF16, FP16,
+    FP32 plain; FP32 accumulation, compositing and Adam in all) maps the same keyframe
+    store from the library's seeded initial parameters; returns rays/s per form."""
+    import numpy as np
+    import torch
+    import synth
+    from synth.multiroom import make_multiroom, multiroom_poses, occupancy_bits_torch, render_keyframes_torch
+    from paper_2210_13641_gb300 import NerfMap
+    K = np.array([600.0 * W / 1200, 600.0 * H / 680, W / 2.0, H / 2.0], np.float32)
+    t0 = time.perf_counter()
+    room = make_multiroom(seed)
+    poses = multiroom_poses(room, n_kf, seed=seed + 1)
+    cfg0 = synth.config_c5("fp32")
+    bits = occupancy_bits_torch(room, cfg0.occ_res, cfg0.grid_origin, cfg0.grid_inv_size)
+    src = list(render_keyframes_torch(room, poses, W, H, K, seed=seed + 2))
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    out = {"workload": f"multi-room 20x20x3 m (16 rooms, 128 primitives), {n_kf} keyframes {W}x{H}, "
+                       f"L=16 F=2 T=2^22 N_min=16 N_max=8192, 256^3 occupancy, {rays} rays/step, "
+                       "<=128 samples/ray (Delta=|diag|/4096)",
+           "keyframe_generation_s": gen_s, "occupied_cells": float(np.unpackbits(bits).mean())}
+    stream = torch.cuda.current_stream().cuda_stream
+    for prec in ("bf16", "fp16", "fp32"):
+        cfg = synth.config_c5(prec)
+        m = NerfMap(cfg, occ_every=0)
+        m.set_occupancy(bits)
+        for kf, rgb, depth, var in src:
+            m.add_keyframe(kf, rgb=rgb, depth=depth, var=var, stream=stream)
+        for i in range(warmup):
+            m.step(rays, seed=seed + i, want_loss=False, stream=stream)
+        torch.cuda.synchronize()
+        m.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(steps):
+            m.step(rays, seed=seed + 100 + i, want_loss=False, stream=stream)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = m.profile_read()
+        st = m.stats()
+        out[prec] = {"value": rays / (ms / 1e3), "unit": "rays/s", "ms_per_step": ms,
+                     "samples_per_step": st.n_samples, "mean_samples_per_ray": st.n_samples / rays,
+                     "phase_ms_per_step": {k: v["ms"] / max(v["count"], 1) for k, v in prof.items() if v["count"]}}
+        m.close()
+    del src
+    torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------- serving
@@ -539,6 +597,9 @@ def main():
     serving = None
     if not args.no_serving and rank == 0:
         serving = {p: serving_benchmark(p, kfs, bits, args.serving_seconds) for p in (args.precision, "fp32")}
+    large = None
+    if not args.no_large_map and rank == 0:
+        large = large_map_benchmark(n_kf=args.large_map_keyframes)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -554,6 +615,8 @@ def main():
                 "gpu_launches": int(launches), "forms": forms}
         if serving:
             line["serving"] = serving
+        if large:
+            line["large_map"] = large
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

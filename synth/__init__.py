@@ -27,3 +27,9 @@ from .room import (  # noqa: F401
     room_occupancy_bits,
     room_spline_poses,
 )
+from .multiroom import (  # noqa: F401
+    make_multiroom,
+    multiroom_poses,
+    render_keyframes_torch,
+    occupancy_bits_torch,
+)
