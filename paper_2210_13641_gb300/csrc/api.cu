@@ -150,6 +150,7 @@ int ensure_step_bufs(map_scene* h, uint32_t n_rays) {
         {(void**)&b.dsig_rgb, sizeof(float4) * cs},
         {(void**)&b.ray_out, sizeof(float) * 5 * cap},
         {(void**)&b.loss, 64},
+        {(void**)&b.partials, sizeof(float) * 4 * kCompositeMaxBlocks},
         {(void**)&b.err, 64},
     };
     if (need_feat) reqs.push_back({(void**)&b.feat, sizeof(float) * kEnc * cs});

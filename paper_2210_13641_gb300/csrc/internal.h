@@ -21,6 +21,8 @@ struct KfDesc {
 // Ray batch, structure of arrays: 11 planes of `cap` floats.
 enum RayPlane { kOx = 0, kOy, kOz, kDx, kDy, kDz, kIr, kIg, kIb, kD, kV, kRayPlanes };
 
+constexpr uint32_t kCompositeMaxBlocks = 4096;
+
 struct StepBufs {
     float* rays;            // [kRayPlanes][cap_rays]
     uint32_t cap_rays;
@@ -33,7 +35,8 @@ struct StepBufs {
     float4* dsig_rgb;       // [cap_samples] dL/dsigma, dL/dr, dL/dg, dL/db (w_i while compositing)
     float* feat;            // [cap_samples][32] stored encodings (FP32)
     float* ray_out;         // [5][cap_rays] I*r, I*g, I*b, D*, acc
-    float* loss;            // [1] + partial
+    float* loss;            // [0] batch loss, [1] [2] largest seeds (FP32 bits), [3] block counter
+    float* partials;        // [kCompositeMaxBlocks][4] per-block sums of the compositing kernel
     uint32_t* err;          // [1]
     uint64_t cap_samples;
 };

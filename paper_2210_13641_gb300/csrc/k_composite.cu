@@ -1,107 +1,227 @@
 // k_composite.cu - alpha compositing of colour and expected depth (Sec. 3.2,
 // Eq. transmittance), the mapping loss of Eq. (mapping_loss) and its gradient with
-// respect to each sample's density and colour (steps a7-a9).  FP32, one thread per
-// ray over that ray's contiguous samples.
+// respect to each sample's density and colour (steps a7-a9).  FP32, one warp per
+// ray: the ray's contiguous samples are taken 32 at a time (coalesced), the
+// transmittance exponent is a warp prefix sum carried from chunk to chunk, and the
+// backward's suffix sums are warp suffix scans over the chunks in reverse order.
 #include "internal.h"
 
 namespace nm {
 
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCompositeWarps = 8;  // warps (rays in flight) per block
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+__device__ __forceinline__ float warp_max(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(kFull, x, o));
+    return x;
+}
+
+// Inclusive prefix sum over lanes 0..lane.
+__device__ __forceinline__ float warp_prefix(float x, uint32_t lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(kFull, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    return x;
+}
+
+// Inclusive suffix sum over lanes lane..31.
+__device__ __forceinline__ float warp_suffix(float x, uint32_t lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_down_sync(kFull, x, o);
+        if (lane + (uint32_t)o < 32u) x += y;
+    }
+    return x;
+}
+
+}  // namespace
+
 // Forward: alpha_i = 1 - exp(-sigma_i delta), T_i = exp(-sum_{j<i} sigma_j delta),
 // w_i = T_i alpha_i; I* = sum w_i c_i, D* = sum w_i t_i, acc = sum w_i.
 // Loss per ray: ||I - I*||^2 + lambda_D (D - D*)^2 / Sigma_D; the batch loss is the
-// mean over rays.  Backward (reverse pass over the ray's samples, suffix sums
-// S_i = sum_{j>i} w_j c_j and the same with t): dL/dc_i = w_i g_I and
+// mean over rays.  Backward (suffix sums S_i = sum_{j>i} w_j c_j and the same with
+// t, taken as suffix scans, never as a total minus a prefix): dL/dc_i = w_i g_I and
 // dL/dsigma_i = delta (g_I . (T_{i+1} c_i - S^c_i) + g_D (T_{i+1} t_i - S^d_i)), with
 // g_I = -2 (I - I*) / R, g_D = -2 lambda_D (D - D*) / (Sigma_D R).
 // loss[0] receives the batch loss; loss[1] and loss[2] the largest density and colour
 // seed magnitudes over samples (FP32 bits), from which the tensor-core backward picks
-// its gradient scales.
+// its gradient scales.  In the forward-only form (render) a ray stops at the first
+// sample whose transmittance is below t_min.  scratch holds (w_i, T_{i+1}) between
+// the two passes and then (dL/dsigma_i, dL/dc_i).
 template <bool kBackward>
-__global__ void k_composite(DevCfg c, uint32_t n_rays, const float* __restrict__ rays, uint32_t cap,
-                            const uint32_t* __restrict__ offsets, const float* __restrict__ ts,
-                            const float4* __restrict__ sig_rgb, float4* __restrict__ scratch,
-                            float* __restrict__ ray_out, float* __restrict__ loss) {
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    float l = 0.f;
+__global__ void __launch_bounds__(kCompositeWarps * 32) k_composite(
+    DevCfg c, uint32_t n_rays, const float* __restrict__ rays, uint32_t cap, const uint32_t* __restrict__ offsets,
+    const float* __restrict__ ts, const float4* __restrict__ sig_rgb, float4* __restrict__ scratch,
+    float* __restrict__ ray_out, float* __restrict__ loss, float* __restrict__ partials) {
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const uint32_t n_warps = gridDim.x * kCompositeWarps;
+    const float delta = c.step_t;
+    float l = 0.f;     // this warp's loss sum (lane 0)
     float gmax = 0.f;  // largest per-sample density seed |dL/dsigma * sigma|
     float cmax = 0.f;  // largest per-sample colour seed |dL/dc|
-    if (r < n_rays) {
+    for (uint32_t r = blockIdx.x * kCompositeWarps + wib; r < n_rays; r += n_warps) {
         const uint32_t a = offsets[r], b = offsets[r + 1];
-        const float delta = c.step_t;
-        float run = 0.f, Ir = 0.f, Ig = 0.f, Ib = 0.f, Dh = 0.f, acc = 0.f;
-        for (uint32_t s = a; s < b; ++s) {
-            const float T = expf(-run);
-            if (!kBackward && T < c.t_min) break;
-            const float4 v = sig_rgb[s];
+        float carry = 0.f;  // sum of sigma delta over the earlier chunks
+        float Ir = 0.f, Ig = 0.f, Ib = 0.f, Dh = 0.f, acc = 0.f;
+        for (uint32_t base = a; base < b; base += 32) {
+            const uint32_t s = base + lane;
+            const bool in = s < b;
+            const float4 v = in ? sig_rgb[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float t = in ? ts[s] : 0.f;
             const float tau = v.x * delta;
-            const float w = T * -expm1f(-tau);
+            const float incl = warp_prefix(tau, lane);
+            float excl = __shfl_up_sync(kFull, incl, 1);
+            if (lane == 0) excl = 0.f;
+            const float T = expf(-(carry + excl));
+            bool live = in;
+            if (!kBackward) live = live && !(T < c.t_min);
+            const float w = live ? T * -expm1f(-tau) : 0.f;
             Ir += w * v.y;
             Ig += w * v.z;
             Ib += w * v.w;
-            Dh += w * ts[s];
+            Dh += w * t;
             acc += w;
-            run += tau;
-            if (kBackward) scratch[s] = make_float4(w, expf(-run), 0.f, 0.f);
+            if (kBackward && in) scratch[s] = make_float4(w, expf(-(carry + incl)), 0.f, 0.f);
+            carry += __shfl_sync(kFull, incl, 31);
+            if (!kBackward && __any_sync(kFull, in && T < c.t_min)) break;
         }
-        ray_out[0 * cap + r] = Ir;
-        ray_out[1 * cap + r] = Ig;
-        ray_out[2 * cap + r] = Ib;
-        ray_out[3 * cap + r] = Dh;
-        ray_out[4 * cap + r] = acc;
+        Ir = warp_sum(Ir);
+        Ig = warp_sum(Ig);
+        Ib = warp_sum(Ib);
+        Dh = warp_sum(Dh);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            ray_out[0 * cap + r] = Ir;
+            ray_out[1 * cap + r] = Ig;
+            ray_out[2 * cap + r] = Ib;
+            ray_out[3 * cap + r] = Dh;
+            ray_out[4 * cap + r] = acc;
+        }
         if (kBackward) {
             const float er = rays[kIr * cap + r] - Ir;
             const float eg = rays[kIg * cap + r] - Ig;
             const float eb = rays[kIb * cap + r] - Ib;
             const float ed = rays[kD * cap + r] - Dh;
             const float V = rays[kV * cap + r];
-            l = er * er + eg * eg + eb * eb + c.lambda_d * ed * ed / V;
+            if (lane == 0) l += er * er + eg * eg + eb * eb + c.lambda_d * ed * ed / V;
             const float inv_n = 1.f / (float)n_rays;
             const float gr = -2.f * er * inv_n, gg = -2.f * eg * inv_n, gb = -2.f * eb * inv_n;
             const float gd = -2.f * c.lambda_d * ed / V * inv_n;
-            float Sr = 0.f, Sg = 0.f, Sb = 0.f, Sd = 0.f;
-            for (uint32_t s = b; s-- > a;) {
-                const float4 v = sig_rgb[s];
-                const float4 q = scratch[s];
-                const float w = q.x, Tn = q.y, t = ts[s];
-                const float dsig = delta * (gr * (Tn * v.y - Sr) + gg * (Tn * v.z - Sg) +
-                                            gb * (Tn * v.w - Sb) + gd * (Tn * t - Sd));
-                scratch[s] = make_float4(dsig, w * gr, w * gg, w * gb);
-                gmax = fmaxf(gmax, fabsf(dsig * v.x));
-                cmax = fmaxf(cmax, fmaxf(fabsf(w * gr), fmaxf(fabsf(w * gg), fabsf(w * gb))));
-                Sr += w * v.y;
-                Sg += w * v.z;
-                Sb += w * v.w;
-                Sd += w * t;
+            float Sr = 0.f, Sg = 0.f, Sb = 0.f, Sd = 0.f;  // suffix sums of the later chunks
+            if (b > a) {
+                for (uint32_t base = a + ((b - a - 1) & ~31u);; base -= 32) {
+                    const uint32_t s = base + lane;
+                    const bool in = s < b;
+                    const float4 v = in ? sig_rgb[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 q = in ? scratch[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float t = in ? ts[s] : 0.f;
+                    const float w = q.x, Tn = q.y;
+                    const float xr = warp_suffix(w * v.y, lane), xg = warp_suffix(w * v.z, lane);
+                    const float xb = warp_suffix(w * v.w, lane), xd = warp_suffix(w * t, lane);
+                    float nr = __shfl_down_sync(kFull, xr, 1), ng = __shfl_down_sync(kFull, xg, 1);
+                    float nb = __shfl_down_sync(kFull, xb, 1), nd = __shfl_down_sync(kFull, xd, 1);
+                    if (lane == 31) nr = ng = nb = nd = 0.f;
+                    const float dsig = delta * (gr * (Tn * v.y - (Sr + nr)) + gg * (Tn * v.z - (Sg + ng)) +
+                                                gb * (Tn * v.w - (Sb + nb)) + gd * (Tn * t - (Sd + nd)));
+                    if (in) {
+                        scratch[s] = make_float4(dsig, w * gr, w * gg, w * gb);
+                        gmax = fmaxf(gmax, fabsf(dsig * v.x));
+                        cmax = fmaxf(cmax, fmaxf(fabsf(w * gr), fmaxf(fabsf(w * gg), fabsf(w * gb))));
+                    }
+                    Sr += __shfl_sync(kFull, xr, 0);
+                    Sg += __shfl_sync(kFull, xg, 0);
+                    Sb += __shfl_sync(kFull, xb, 0);
+                    Sd += __shfl_sync(kFull, xd, 0);
+                    if (base == a) break;
+                }
             }
         }
     }
     if (kBackward) {
-        // mean over rays: warp sum, one atomic per warp
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            l += __shfl_xor_sync(0xffffffffu, l, o);
-            gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-            cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+        // Per block: warp sums / maxima through shared memory into partials[block];
+        // the last block to finish reduces all partials in a fixed order, so the
+        // batch loss does not depend on the order in which blocks finish.
+        __shared__ float sl[kCompositeWarps], sg[kCompositeWarps], sc[kCompositeWarps];
+        __shared__ bool last;
+        l = warp_sum(l);
+        gmax = warp_max(gmax);
+        cmax = warp_max(cmax);
+        if (lane == 0) {
+            sl[wib] = l;
+            sg[wib] = gmax;
+            sc[wib] = cmax;
         }
-        if ((threadIdx.x & 31) == 0) {
-            if (l != 0.f) atomicAdd(loss, l / (float)n_rays);
-            // non-negative floats order like their bit patterns
-            if (gmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(loss) + 1, __float_as_uint(gmax));
-            if (cmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(loss) + 2, __float_as_uint(cmax));
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float L = 0.f, G = 0.f, C = 0.f;
+            for (int i = 0; i < kCompositeWarps; ++i) {
+                L += sl[i];
+                G = fmaxf(G, sg[i]);
+                C = fmaxf(C, sc[i]);
+            }
+            partials[4 * blockIdx.x + 0] = L;
+            partials[4 * blockIdx.x + 1] = G;
+            partials[4 * blockIdx.x + 2] = C;
+            __threadfence();
+            const uint32_t ticket = atomicAdd(reinterpret_cast<unsigned int*>(loss) + 3, 1u);
+            last = ticket == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (last && wib == 0) {
+            __threadfence();
+            float L = 0.f, G = 0.f, C = 0.f;
+            for (uint32_t i = lane; i < gridDim.x; i += 32) {
+                L += __ldcg(partials + 4 * i + 0);
+                G = fmaxf(G, __ldcg(partials + 4 * i + 1));
+                C = fmaxf(C, __ldcg(partials + 4 * i + 2));
+            }
+            L = warp_sum(L);
+            G = warp_max(G);
+            C = warp_max(C);
+            if (lane == 0) {
+                loss[0] = L / (float)n_rays;
+                // non-negative floats order like their bit patterns
+                reinterpret_cast<unsigned int*>(loss)[1] = __float_as_uint(G);
+                reinterpret_cast<unsigned int*>(loss)[2] = __float_as_uint(C);
+                reinterpret_cast<unsigned int*>(loss)[3] = 0u;
+            }
         }
     }
 }
 
 void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const StepBufs& b,
                       cudaStream_t s) {
-    const uint32_t grid = (n_rays + 127) / 128;
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 148;
+    }
+    uint32_t grid = (n_rays + kCompositeWarps - 1) / kCompositeWarps;
+    uint32_t cap = (uint32_t)n_sm * 8;  // persistent warps loop over the rays
+    if (cap > kCompositeMaxBlocks) cap = kCompositeMaxBlocks;
+    if (grid > cap) grid = cap;
+    if (grid == 0) grid = 1;
     if (backward) {
-        cudaMemsetAsync(b.loss, 0, 3 * sizeof(float), s);
-        k_composite<true><<<grid, 128, 0, s>>>(c, n_rays, b.rays, b.cap_rays, b.offsets, b.t,
-                                               b.sig_rgb, b.dsig_rgb, b.ray_out, b.loss);
+        cudaMemsetAsync(b.loss, 0, 4 * sizeof(float), s);
+        k_composite<true><<<grid, kCompositeWarps * 32, 0, s>>>(c, n_rays, b.rays, b.cap_rays, b.offsets, b.t,
+                                                                b.sig_rgb, b.dsig_rgb, b.ray_out, b.loss,
+                                                                b.partials);
     } else {
-        k_composite<false><<<grid, 128, 0, s>>>(c, n_rays, b.rays, b.cap_rays, b.offsets, b.t,
-                                                b.sig_rgb, nullptr, b.ray_out, nullptr);
+        k_composite<false><<<grid, kCompositeWarps * 32, 0, s>>>(c, n_rays, b.rays, b.cap_rays, b.offsets, b.t,
+                                                                 b.sig_rgb, nullptr, b.ray_out, nullptr, nullptr);
     }
 }
 
