@@ -122,28 +122,38 @@ void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t 
 }
 
 // ---------------------------------------------------------------- march
-// One pass over the steps of each ray: the t of every retained step goes to the
-// ray's slot row (max_samples floats per ray, in step order) and the count to
+// One pass over the steps of each ray, one warp per ray: the 32 lanes test 32
+// consecutive steps at a time and a ballot gives each retained step its place in
+// the ray's slot row (max_samples floats per ray, in step order); the count goes to
 // counts[r].  After the scan, k_compact copies each ray's row to its offset (one
 // warp per ray, coalesced) and writes the ray index beside each sample.
 __global__ void k_march(DevCfg c, const uint32_t* __restrict__ bits, uint32_t n_rays,
                         const float* __restrict__ rays, uint32_t cap, uint32_t* __restrict__ counts,
                         float* __restrict__ slots) {
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rays) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= n_rays) return;  // whole warps
     const float3 o = make_float3(rays[kOx * cap + r], rays[kOy * cap + r], rays[kOz * cap + r]);
     const float3 d = make_float3(rays[kDx * cap + r], rays[kDy * cap + r], rays[kDz * cap + r]);
-    uint32_t n = 0;
     float* row = slots + (size_t)r * c.max_samples;
     uint32_t i_lo, i_hi;
     box_step_range(c, o, d, i_lo, i_hi);
-    for (uint32_t i = i_lo; i < i_hi && n < c.max_samples; ++i) {
-        const float t = sample_t(c, i);
-        const float3 x = grid_pos(c, o, d, t);
-        if (!in_box(c, x) || !occupied(c, bits, x)) continue;
-        row[n++] = t;
+    uint32_t n = 0;
+    for (uint32_t i0 = i_lo; i0 < i_hi && n < c.max_samples; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        bool keep = false;
+        float t = 0.f;
+        if (i < i_hi) {
+            t = sample_t(c, i);
+            const float3 x = grid_pos(c, o, d, t);
+            keep = in_box(c, x) && occupied(c, bits, x);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, keep);
+        const uint32_t pos = n + __popc(m & ((1u << lane) - 1u));
+        if (keep && pos < c.max_samples) row[pos] = t;
+        n += __popc(m);
     }
-    counts[r] = n;
+    if (lane == 0) counts[r] = n < c.max_samples ? n : c.max_samples;
 }
 
 __global__ void k_compact(uint32_t n_rays, uint32_t max_samples, const uint32_t* __restrict__ offsets,
@@ -247,7 +257,7 @@ void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, co
                   cudaStream_t s) {
     // slot rows live in the (not yet used) per-sample colour buffer: cap_samples floats
     float* slots = reinterpret_cast<float*>(b.sig_rgb);
-    k_march<<<(n_rays + 127) / 128, 128, 0, s>>>(c, occ_bits, n_rays, b.rays, b.cap_rays, b.counts, slots);
+    k_march<<<(n_rays + 7) / 8, 256, 0, s>>>(c, occ_bits, n_rays, b.rays, b.cap_rays, b.counts, slots);
     const uint32_t n_tiles = (n_rays + kScanTile - 1) / kScanTile;  // <= kScanTile (n <= 2^24)
     k_scan_tiles<<<n_tiles, kScanThreads, 0, s>>>(b.counts, n_rays, b.offsets, b.block_sums);
     k_scan_top<<<1, kScanThreads, 0, s>>>(b.block_sums, n_tiles, b.offsets + n_rays);
