@@ -232,7 +232,8 @@ def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, 
 
 # ----------------------------------------------------------------- large map
 
-def large_map_benchmark(n_kf=2000, W=1200, H=680, rays=1 << 20, steps=5, warmup=2, seed=0):
+def large_map_benchmark(n_kf=2000, W=1200, H=680, rays=1 << 20, steps=5, warmup=2, seed=0,
+                        precisions=("bf16", "fp16", "fp32")):
     """The large-map configuration: L=16, T=2^22, N 16..8192, 256^3 occupancy over a
     20x20x3 m multi-room floor (16 rooms, doorways, 128 primitives), `n_kf` keyframes
     of W x H rendered on the GPU, `rays` rays per step.  Each MLP form (BF16, FP16,
@@ -257,7 +258,7 @@ def large_map_benchmark(n_kf=2000, W=1200, H=680, rays=1 << 20, steps=5, warmup=
                        "<=128 samples/ray (Delta=|diag|/4096)",
            "keyframe_generation_s": gen_s, "occupied_cells": float(np.unpackbits(bits).mean())}
     stream = torch.cuda.current_stream().cuda_stream
-    for prec in ("bf16", "fp16", "fp32"):
+    for prec in precisions:
         cfg = synth.config_c5(prec)
         m = NerfMap(cfg, occ_every=0)
         m.set_occupancy(bits)

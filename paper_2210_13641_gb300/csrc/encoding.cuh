@@ -127,9 +127,10 @@ __device__ __forceinline__ void hash_scatter(const DevCfg& c, float2* __restrict
 // A level whose 32 cells are all different skips the reduction.
 // The level loop is unrolled by two only (two levels' shuffles in flight): the fully
 // unrolled form's code did not fit the instruction cache next to the tensor-core
-// layer chain of the backward kernel.  A run is cut every 8 lanes, so the reduction
-// takes at most 3 rounds (a few more reductions for long runs of the coarse levels,
-// measured cheaper than 5 rounds; cutting every 4 lanes measured far slower).
+// layer chain of the backward kernel.  Runs are not cut short to save reduction
+// rounds: every extra head costs 8 reductions, which the large map's HBM-resident
+// tables pay dearly (cutting runs every 8 lanes: -1 % on a 64 MB table, +20 % on a
+// 512 MB one).
 __device__ __forceinline__ void hash_scatter_warp(const DevCfg& c, float2* __restrict__ gtables,
                                                   float3 x, const float* df, bool valid) {
     const uint32_t Tmask = c.T - 1;
@@ -148,7 +149,7 @@ __device__ __forceinline__ void hash_scatter_warp(const DevCfg& c, float2* __res
         const float g0 = valid ? df[2 * l] : 0.f, g1 = valid ? df[2 * l + 1] : 0.f;
         const uint64_t key = valid ? (((uint64_t)cz << 42) | ((uint64_t)cy << 21) | cx) : ~(uint64_t)lane;
         const uint64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-        const bool head = (lane & 7u) == 0 || prev != key;   // runs of at most 8 lanes
+        const bool head = lane == 0 || prev != key;
         const uint32_t heads = __ballot_sync(0xffffffffu, head);
         float v[16];
 #pragma unroll
