@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-serving", action="store_true", help="skip the multi-scene serving measurement")
     p.add_argument("--no-large-map", action="store_true", help="skip the large-map precision comparison")
     p.add_argument("--large-map-keyframes", type=int, default=2000)
+    p.add_argument("--ablation", action="store_true", help="also run the Sigma_D-weighting ablation (about 1 min)")
     p.add_argument("--serving-seconds", type=float, default=6.0)
     p.add_argument("--rays", type=int, default=N_RAYS)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -179,13 +180,19 @@ class ClockSampler:
 # ----------------------------------------------------------------- quality
 
 def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, H=120, seed=0,
-                sigma_floor=0.2, ray_seed=0):
+                sigma_floor=0.2, ray_seed=0, outlier_frac=0.0, depth_weighting="sigma_d"):
     """Fits the room from noisy 320x240 keyframes (depth noise sigma_d >= sigma_floor
     metres) along a smooth seeded camera path
     (a Catmull-Rom spline through 8 interior points) for `steps` mapping steps and
     returns PSNR (dB) and depth-L1 (m, along the ray) of held-out views of the same
     path (every `every`-th pose, offset by half a period, never trained on) against
-    the analytic ground truth, before and after training."""
+    the analytic ground truth, before and after training.
+
+    outlier_frac: fraction of keyframe pixels with a gross depth error reported with
+    sigma_d = 1 m.  depth_weighting: "sigma_d" (the paper's loss, each pixel's depth
+    residual divided by its variance Sigma_D), "raw" (every pixel's variance replaced
+    by the median variance of the non-outlier pixels: the same overall depth weight,
+    no down-weighting of the outliers) or "none" (lambda_D = 0, colour only)."""
     import numpy as np
     import synth
     from paper_2210_13641_gb300 import NerfMap, pack_params
@@ -195,7 +202,16 @@ def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, 
     held = set(range(every // 2, n_poses, every))
     train = [p for i, p in enumerate(poses) if i not in held]
     kfs = synth.room_keyframes(room, len(train), seed=seed + 1, W=320, H=240, K=(262.5, 262.5, 160.0, 120.0),
-                               poses=train, sigma_floor=sigma_floor)
+                               poses=train, sigma_floor=sigma_floor, outlier_frac=outlier_frac)
+    if depth_weighting == "raw":
+        good = np.concatenate([k.var[k.var < 1.0].ravel() for k in kfs])
+        v0 = np.float32(np.median(good))
+        for k in kfs:
+            k.var = np.full_like(k.var, v0)
+    elif depth_weighting == "none":
+        cfg = cfg.replace(lambda_d=np.float32(0.0))
+    elif depth_weighting != "sigma_d":
+        raise ValueError(depth_weighting)
     bits = synth.room_occupancy_bits(room, cfg.occ_res, cfg.grid_origin, cfg.grid_inv_size)
     Kv = (525.0 * W / 640, 525.0 * H / 480, W / 2.0, H / 2.0)
     views = synth.room_keyframes(room, len(held), seed=seed + 9, W=W, H=H, K=Kv, noise_k=0.0,
@@ -226,8 +242,26 @@ def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, 
     p1, d1 = evaluate()
     m.close()
     return {"precision": precision, "steps": steps, "rays_per_step": rays, "train_keyframes": len(kfs),
+            "outlier_frac": outlier_frac, "depth_weighting": depth_weighting,
             "heldout_views": len(views), "psnr_db": p1, "depth_l1_m": d1, "psnr_db_init": p0,
             "depth_l1_m_init": d0, "final_loss": loss, "train_s": t}
+
+
+# ----------------------------------------------------------------- depth weighting
+
+def sigma_d_ablation(precision="fp16", steps=3000, outlier_frac=0.2, seeds=(0, 1)):
+    """The paper's depth-weighting ablation on the synthetic room: keyframes with
+    `outlier_frac` of the pixels carrying a gross depth error reported with
+    sigma_d = 1 m; held-out PSNR / depth-L1 of the Sigma_D-weighted depth loss, the
+    raw depth loss (all pixels at the median good-pixel variance) and colour only."""
+    out = {"outlier_frac": outlier_frac, "steps": steps, "precision": precision}
+    for mode in ("sigma_d", "raw", "none"):
+        runs = [quality_run(precision, steps=steps, ray_seed=s, outlier_frac=outlier_frac, depth_weighting=mode,
+                            sigma_floor=0.05) for s in seeds]
+        out[mode] = {"psnr_db": [r["psnr_db"] for r in runs], "depth_l1_m": [r["depth_l1_m"] for r in runs],
+                     "psnr_db_mean": sum(r["psnr_db"] for r in runs) / len(runs),
+                     "depth_l1_m_mean": sum(r["depth_l1_m"] for r in runs) / len(runs)}
+    return out
 
 
 # ----------------------------------------------------------------- large map
@@ -601,6 +635,7 @@ def main():
     large = None
     if not args.no_large_map and rank == 0:
         large = large_map_benchmark(n_kf=args.large_map_keyframes)
+    ablation = sigma_d_ablation(args.precision) if args.ablation and rank == 0 else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -618,6 +653,8 @@ def main():
             line["serving"] = serving
         if large:
             line["large_map"] = large
+        if ablation:
+            line["sigma_d_ablation"] = ablation
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

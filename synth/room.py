@@ -145,10 +145,14 @@ def _inside_prims(room: Room, p: np.ndarray, margin: float) -> np.ndarray:
 
 def room_keyframes(room: Room, n: int, seed: int = 0, W: int = 640, H: int = 480,
                    K=(525.0, 525.0, 320.0, 240.0), noise_k: float = 0.01,
-                   poses=None, first_id: int = 0, sigma_floor: float = 0.0):
+                   poses=None, first_id: int = 0, sigma_floor: float = 0.0,
+                   outlier_frac: float = 0.0, outlier_range: float = 2.0, outlier_sigma: float = 1.0):
     """`n` keyframes at seeded poses inside the room looking at random interior
     points.  depth = z + N(0, sigma_d^2), sigma_d = max(noise_k * z^2 * U[0.5, 2],
-    sigma_floor), var = sigma_d^2 (z-depth units)."""
+    sigma_floor), var = sigma_d^2 (z-depth units).  With outlier_frac > 0 that
+    fraction of the pixels (drawn independently) gets a gross depth error instead,
+    depth = max(z + U[-outlier_range, outlier_range], 0.1), reported with
+    sigma_d = outlier_sigma (a depth estimator that knows where it is unsure)."""
     rng = np.random.default_rng(seed)
     K = np.asarray(K, np.float32)
     E = room.extent
@@ -169,6 +173,11 @@ def room_keyframes(room: Room, n: int, seed: int = 0, W: int = 640, H: int = 480
         z, rgb = render_room(room, c2w, K, W, H)
         sigma = np.maximum(noise_k * z * z * rng.uniform(0.5, 2.0, size=z.shape), sigma_floor)
         depth = z + rng.normal(size=z.shape) * sigma
+        if outlier_frac > 0.0:
+            bad = rng.uniform(size=z.shape) < outlier_frac
+            depth = np.where(bad, np.maximum(z + rng.uniform(-outlier_range, outlier_range, size=z.shape), 0.1),
+                             depth)
+            sigma = np.where(bad, outlier_sigma, sigma)
         out.append(Keyframe(first_id + k, c2w.astype(np.float32), K, W, H,
                             rgb.astype(np.float32), depth.astype(np.float32),
                             (sigma * sigma).astype(np.float32), depth_is_z=True))
