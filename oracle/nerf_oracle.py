@@ -429,7 +429,7 @@ def composite_backward_ray_abs(sigma, rgb, t, delta, w, Tcum, gI, gD):
 
 # ------------------------------------------------------------------ a10, a11: backward
 
-def field_backward(P: dict, fw: dict, dsigma, drgb, magnitude: bool = False):
+def field_backward(P: dict, fw: dict, dsigma, drgb, magnitude: bool = False, with_dsh: bool = False):
     """Chain rule through the MLPs (a10).  Returns weight gradients and dL/dfeat.
     magnitude=True (with the absolute-term inputs of composite_backward_ray_abs)
     runs the same chain on |W| and on activation magnitudes (each activation
@@ -463,6 +463,8 @@ def field_backward(P: dict, fw: dict, dsigma, drgb, magnitude: bool = False):
     da1 = dh1 * fw["m1"]
     g["W1"] = da1.T @ fw["feat"]
     dfeat = da1 @ W["W1"]
+    if with_dsh:
+        return g, dfeat, dx3[:, P["W2"].shape[0]:]      # dL/d(SH inputs of the colour MLP)
     return g, dfeat
 
 
@@ -615,3 +617,155 @@ def render(cfg, P, c2w, K, W, H, occ_bits=None, level_res=None, t_min=None, deci
     I_hat, D_hat, acc, _, _ = composite(ray_id, fw["sigma"], fw["rgb"], t.astype(np.float64),
                                         float(cfg.step), W * H, t_min)
     return I_hat, D_hat, acc
+
+
+# ------------------------------------------------------------------ joint pose refinement
+# The mapping loss is minimised over the keyframe poses T as well as the map (Sec. 3.2:
+# L_M(T, Theta)).  Here the gradient with respect to each keyframe pose, for a batch
+# whose sample list (ray id, t) is held fixed: a pose moves every sample of its rays
+# (p = o + t d) and turns their view directions, while the march's keep/drop
+# decisions are integers that do not move.  Pose perturbation: left, in the world
+# frame, T <- exp(xi) T with xi = (rho, phi): p -> R(phi) p + rho, so o -> o + rho +
+# phi x o and d -> d + phi x d to first order, and
+#   dL/drho = sum_rays dL/do,   dL/dphi = sum_rays (o x dL/do + d x dL/dd).
+
+def sh_deg4_jacobian(d: np.ndarray) -> np.ndarray:
+    """d/dd of the 16 SH values of sh_deg4 (each a polynomial in x, y, z): [S, 16, 3]."""
+    x, y, z = d[:, 0].astype(np.float64), d[:, 1].astype(np.float64), d[:, 2].astype(np.float64)
+    pi = math.pi
+    a1 = math.sqrt(3 / (4 * pi))
+    b = 0.5 * math.sqrt(15 / pi)
+    c = 0.25 * math.sqrt(5 / pi)
+    e = 0.25 * math.sqrt(15 / pi)
+    f = 0.25 * math.sqrt(35 / (2 * pi))
+    g = 0.5 * math.sqrt(105 / pi)
+    h = 0.25 * math.sqrt(21 / (2 * pi))
+    i = 0.25 * math.sqrt(7 / pi)
+    j = 0.25 * math.sqrt(105 / pi)
+    zero = np.zeros_like(x)
+    one = np.ones_like(x)
+    J = np.stack([
+        np.stack([zero, zero, zero], -1),
+        np.stack([zero, -a1 * one, zero], -1),
+        np.stack([zero, zero, a1 * one], -1),
+        np.stack([-a1 * one, zero, zero], -1),
+        np.stack([b * y, b * x, zero], -1),
+        np.stack([zero, -b * z, -b * y], -1),
+        np.stack([zero, zero, 6 * c * z], -1),
+        np.stack([-b * z, zero, -b * x], -1),
+        np.stack([2 * e * x, -2 * e * y, zero], -1),
+        np.stack([-6 * f * x * y, -f * (3 * x * x - 3 * y * y), zero], -1),
+        np.stack([g * y * z, g * x * z, g * x * y], -1),
+        np.stack([zero, -h * (5 * z * z - 1), -10 * h * y * z], -1),
+        np.stack([zero, zero, i * (15 * z * z - 3)], -1),
+        np.stack([-h * (5 * z * z - 1), zero, -10 * h * x * z], -1),
+        np.stack([2 * j * x * z, -2 * j * y * z, j * (x * x - y * y)], -1),
+        np.stack([-f * (3 * x * x - 3 * y * y), 6 * f * x * y, zero], -1),
+    ], axis=1)
+    return J
+
+
+def hash_encode_dx(cfg, level_res, tables: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """d(features)/dx of the grid encoding at x [S,3] (the derivative of the
+    trilinear interpolation inside each cell): [S, enc_width, 3].  With
+    w_k = prod_a (b_a ? w_a : 1 - w_a) and w_a = x_a N - c_a,
+    dw_k/dx_a = N (b_a ? 1 : -1) prod_{a' != a} (b_a' ? w_a' : 1 - w_a')."""
+    S = x.shape[0]
+    L, F, T = cfg.n_levels, cfg.n_features, cfg.table_size
+    out = np.zeros((S, cfg.enc_width, 3))
+    tab = tables.astype(np.float64)
+    for l in range(L):
+        N = level_res[l]
+        c, w = grid_cell_f32(x, N)
+        for k in range(8):
+            bk = CORNERS[k]
+            fac = np.where(bk[None, :] == 1, w, 1.0 - w)          # [S, 3]
+            ik = vertex_index(c + bk[None, :], N, T)
+            vals = tab[l, ik]                                       # [S, F]
+            for a in range(3):
+                others = np.prod(np.delete(fac, a, axis=1), axis=1)
+                dw = N * (1.0 if bk[a] == 1 else -1.0) * others
+                out[:, l * F:(l + 1) * F, a] += dw[:, None] * vals
+    return out
+
+
+def pose_gradients(cfg, P, keyframes, n_rays, seed, step, occ_bits=None, level_res=None, decide_in=None):
+    """Gradient of the batch loss with respect to each keyframe pose (left world-frame
+    perturbation, see above) for the batch of forward_backward, its sample list held
+    fixed.  Returns dict(loss, pose_grads [n_kf, 6] = (dL/drho, dL/dphi) per keyframe,
+    g_o [R, 3], g_d [R, 3] per ray, kf [R])."""
+    fb = forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits=occ_bits, level_res=level_res,
+                          decide_in=decide_in)
+    lr = fb["level_res"]
+    feat, _, _ = hash_encode(cfg, lr, P["tables"], fb["x"])
+    sh = sh_deg4(fb["d"][fb["ray_id"]])
+    dec = relu_decisions(P, feat, sh, decide_in) if decide_in not in (None, "fp32") else None
+    fw = field_forward(P, feat, sh, dec)
+    _, dfeat, dsh = field_backward(P, fw, fb["dsigma"], fb["drgb"], with_dsh=True)
+    dfdx = hash_encode_dx(cfg, lr, P["tables"], fb["x"])             # [S, E, 3]
+    dLdx = np.einsum("se,sea->sa", dfeat, dfdx)                       # [S, 3]
+    dLdp = dLdx * float(cfg.grid_inv_size)
+    Jsh = sh_deg4_jacobian(fb["d"][fb["ray_id"]])                    # [S, 16, 3]
+    dLdd_sh = np.einsum("sk,ska->sa", dsh, Jsh)
+    rid = fb["ray_id"]
+    t = fb["t"].astype(np.float64)
+    g_o = np.zeros((n_rays, 3))
+    g_d = np.zeros((n_rays, 3))
+    np.add.at(g_o, rid, dLdp)
+    np.add.at(g_d, rid, t[:, None] * dLdp + dLdd_sh)
+    o = fb["o"].astype(np.float64)
+    d = fb["d"].astype(np.float64)
+    pg = np.zeros((len(keyframes), 6))
+    np.add.at(pg, fb["kf"], np.concatenate([g_o, np.cross(o, g_o) + np.cross(d, g_d)], axis=1))
+    return dict(loss=fb["loss"], pose_grads=pg, g_o=g_o, g_d=g_d, kf=fb["kf"], fb=fb)
+
+
+def loss_moved_samples(cfg, P, fb, drho, dphi, kf_index, level_res=None):
+    """The batch loss of forward_backward's result `fb` with keyframe `kf_index`
+    moved by the left perturbation (drho, dphi) (rotation by the vector dphi,
+    Rodrigues' formula) and every sample kept at its t: positions and directions of
+    that keyframe's rays move, the sample list and the targets do not.  FP64
+    throughout (for finite differences of pose_gradients)."""
+    lr = fb["level_res"] if level_res is None else level_res
+    o = fb["o"].astype(np.float64).copy()
+    d = fb["d"].astype(np.float64).copy()
+    th = float(np.linalg.norm(dphi))
+    if th > 0:
+        k = np.asarray(dphi, np.float64) / th
+        Kx = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+        R = np.eye(3) + math.sin(th) * Kx + (1 - math.cos(th)) * Kx @ Kx
+    else:
+        R = np.eye(3)
+    sel = fb["kf"] == kf_index
+    o[sel] = o[sel] @ R.T + np.asarray(drho, np.float64)
+    d[sel] = d[sel] @ R.T
+    rid = fb["ray_id"]
+    t = fb["t"].astype(np.float64)
+    p = o[rid] + t[:, None] * d[rid]
+    x = (p - cfg.grid_origin.astype(np.float64)) * float(cfg.grid_inv_size)
+    feat = hash_encode_f64(cfg, lr, P["tables"], x)
+    sh = sh_deg4(d[rid])
+    fw = field_forward(P, feat, sh)
+    n_rays = len(fb["kf"])
+    I_hat, D_hat, _, _, _ = composite(rid, fw["sigma"], fw["rgb"], t, float(cfg.step), n_rays)
+    loss, _ = mapping_loss(I_hat, D_hat, fb["I"], fb["D"], fb["V"], float(cfg.lambda_d))
+    return loss
+
+
+def hash_encode_f64(cfg, level_res, tables, x):
+    """hash_encode with the cell and offset taken in FP64 (for finite differences:
+    a float32 position would swallow the perturbation)."""
+    S = x.shape[0]
+    L, F, T = cfg.n_levels, cfg.n_features, cfg.table_size
+    feat = np.zeros((S, cfg.enc_width))
+    tab = tables.astype(np.float64)
+    for l in range(L):
+        N = level_res[l]
+        q = x * N
+        c = np.minimum(np.floor(q).astype(np.int64), N - 1)
+        w = q - c
+        for k in range(8):
+            bk = CORNERS[k]
+            wk = np.prod(np.where(bk[None, :] == 1, w, 1.0 - w), axis=1)
+            feat[:, l * F:(l + 1) * F] += wk[:, None] * tab[l, vertex_index(c + bk[None, :], N, T)]
+    return feat
