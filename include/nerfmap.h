@@ -58,6 +58,7 @@ extern "C" {
 
 /* map_step flags */
 #define MAP_STEP_NO_UPDATE 1u  /* compute loss and gradients, skip Adam, keep gradients */
+#define MAP_STEP_POSE_GRAD 2u  /* also the gradient of L_M with respect to every keyframe pose */
 
 /*
  * Field and step configuration (copied by map_create).
@@ -208,6 +209,27 @@ int map_get_params(map_handle h, float* dst, size_t n, int mem_kind, void* strea
 int map_set_params(map_handle h, const float* src, size_t n, int mem_kind, void* stream);
 /* Gradient of L_M from the last step (meaningful after MAP_STEP_NO_UPDATE). */
 int map_get_grads(map_handle h, float* dst, size_t n, int mem_kind, void* stream);
+
+/*
+ * Joint pose refinement (Sec. 3.2: L_M is minimised over the keyframe poses T as
+ * well as the map).  After a map_step with MAP_STEP_POSE_GRAD, map_get_pose_grads
+ * writes, for each keyframe slot s < n_kf, dst[6 s .. 6 s + 5] = (dL/drho, dL/dphi):
+ * the gradient of the step's L_M under the left world-frame perturbation
+ * T <- exp(xi) T, xi = (rho, phi) (a point p moves to R(phi) p + rho), with the
+ * step's sample list held fixed.  Keyframes that drew no ray get zeros.  Slots are
+ * numbered in the order keyframes were first added (a replaced kf_id keeps its
+ * slot; map_get_keyframe_ids lists the ids by slot).  n_kf must not exceed the
+ * number of keyframes.  Waits for the stream with host memory.  MAP_EINVAL
+ * without a preceding POSE_GRAD step.
+ */
+int map_get_pose_grads(map_handle h, float* dst, uint32_t n_kf, int mem_kind, void* stream);
+/* The kf_id of each keyframe slot: ids[s] for s < min(n, number of keyframes);
+ * returns the number of keyframes (host memory). */
+int map_get_keyframe_ids(map_handle h, uint32_t* ids, uint32_t n);
+/* Replace the pose of keyframe kf_id (c2w[12], host memory, the layout of
+ * map_add_keyframe), keeping its images; stream ordered.  MAP_EINVAL if the id is
+ * not in the store. */
+int map_set_keyframe_pose(map_handle h, uint32_t kf_id, const float c2w[12], void* stream);
 /* Adam moments m, v (either may be NULL) and a reset of the optimiser state. */
 int map_get_adam(map_handle h, float* m, float* v, size_t n, int mem_kind, void* stream);
 int map_reset_adam(map_handle h, void* stream);

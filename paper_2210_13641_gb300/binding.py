@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libnerfmap.so")
 MAP_OK, MAP_EINVAL, MAP_ENOMEM, MAP_ENOKF, MAP_ETIMEOUT, MAP_ECUDA = 0, -1, -2, -3, -4, -5
 MAP_MEM_HOST, MAP_MEM_DEVICE = 0, 1
 MAP_STEP_NO_UPDATE = 1
+MAP_STEP_POSE_GRAD = 2
 PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2}
 MLP_SHAPES = [("W1", (64, 32)), ("W2", (16, 64)), ("W3", (64, 32)), ("W4", (64, 64)), ("W5", (3, 64))]
 MLP_PARAMS = sum(a * b for _, (a, b) in MLP_SHAPES)
@@ -94,6 +95,10 @@ _SIGS = {
     "map_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     "map_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     "map_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
+    "map_get_pose_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int,
+                                          ctypes.c_void_p]),
+    "map_get_keyframe_ids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]),
+    "map_set_keyframe_pose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "map_get_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                     ctypes.c_int, ctypes.c_void_p]),
     "map_reset_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -320,12 +325,30 @@ class NerfMap:
                                               pr, pd, pv, int(bool(kf.depth_is_z)), kind, _stream(stream)))
 
     # -------------------------------------------------------------- step / render
-    def step(self, n_rays: int, seed: int, no_update: bool = False, want_loss: bool = True, stream=None):
+    def step(self, n_rays: int, seed: int, no_update: bool = False, want_loss: bool = True, stream=None,
+             pose_grad: bool = False):
         loss = ctypes.c_float()
-        flags = MAP_STEP_NO_UPDATE if no_update else 0
+        flags = (MAP_STEP_NO_UPDATE if no_update else 0) | (MAP_STEP_POSE_GRAD if pose_grad else 0)
         self._check(self.lib.map_step(self.h, n_rays, seed, flags,
                                       ctypes.byref(loss) if want_loss else None, _stream(stream)))
         return loss.value if want_loss else None
+
+    def keyframe_ids(self) -> list:
+        n = self.lib.map_get_keyframe_ids(self.h, None, 0)
+        ids = (ctypes.c_uint32 * max(n, 1))()
+        self.lib.map_get_keyframe_ids(self.h, ids, n)
+        return list(ids[:n])
+
+    def pose_grads(self, stream=None) -> np.ndarray:
+        """[n_kf, 6] = (dL/drho, dL/dphi) per keyframe slot of the last POSE_GRAD step."""
+        n = len(self.keyframe_ids())
+        out = np.zeros((n, 6), np.float32)
+        self._check(self.lib.map_get_pose_grads(self.h, out.ctypes.data, n, MAP_MEM_HOST, _stream(stream)))
+        return out
+
+    def set_pose(self, kf_id: int, c2w, stream=None):
+        c2w = np.ascontiguousarray(c2w, np.float32).reshape(12)
+        self._check(self.lib.map_set_keyframe_pose(self.h, kf_id, c2w.ctypes.data, _stream(stream)))
 
     def loss_device_ptr(self) -> int:
         return self.lib.map_loss_device(self.h)

@@ -55,6 +55,11 @@ struct map_scene {
 
     StepBufs bufs{};
     std::vector<void*> buf_allocs;
+    float4* pose_s = nullptr;       // per-sample pose terms (allocated on the first POSE_GRAD step)
+    uint64_t pose_s_cap = 0;
+    float* pose_g = nullptr;        // [pose_g_cap][8] per keyframe slot
+    uint32_t pose_g_cap = 0;
+    bool pose_valid = false;
 
     uint64_t step = 0, n_refresh = 0;
     bool grads_dirty = false;
@@ -429,6 +434,31 @@ int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float
         NM_CUDA(h, cudaMemsetAsync(h->grads, 0, h->n_params * sizeof(float), s));
         h->grads_dirty = false;
     }
+    const bool pose = (flags & MAP_STEP_POSE_GRAD) != 0;
+    h->pose_valid = false;
+    if (pose) {
+        if (h->pose_s_cap < h->bufs.cap_samples) {
+            cudaStreamSynchronize(s);
+            dfree(h, h->pose_s);
+            h->pose_s = nullptr;
+            h->pose_s_cap = 0;
+            rc = dalloc(h, (void**)&h->pose_s, h->bufs.cap_samples * 2 * sizeof(float4));
+            if (rc) return rc;
+            h->pose_s_cap = h->bufs.cap_samples;
+        }
+        if (h->pose_g_cap < h->kfs.size()) {
+            cudaStreamSynchronize(s);
+            dfree(h, h->pose_g);
+            h->pose_g = nullptr;
+            h->pose_g_cap = 0;
+            const uint32_t cap = std::max<uint32_t>(64, (uint32_t)h->kfs.size() * 2);
+            rc = dalloc(h, (void**)&h->pose_g, (size_t)cap * 8 * sizeof(float));
+            if (rc) return rc;
+            h->pose_g_cap = cap;
+        }
+        h->bufs.pose_s = h->pose_s;
+        NM_CUDA(h, cudaMemsetAsync(h->pose_g, 0, h->kfs.size() * 8 * sizeof(float), s));
+    }
     const StepBufs& b = h->bufs;
     rc = phase(h, MAP_PH_RAYGEN, 1, s,
                [&] { launch_ray_gen(h->d_kfs, (uint32_t)h->kfs.size(), seed, h->step, n_rays, b, s); });
@@ -437,11 +467,15 @@ int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float
     if (!rc)
         rc = phase(h, MAP_PH_FIELD_BWD, 1, s, [&] {
             if (h->cfg.precision == MAP_PREC_FP32)
-                launch_field_bwd_fp32(h->dc, h->params, h->grads, n_rays, b, h->n_sm, s);
+                launch_field_bwd_fp32(h->dc, h->params, h->grads, n_rays, b, h->n_sm, s, pose);
             else
                 launch_field_bwd_tc(h->dc, h->params, h->grads, n_rays, b, h->cfg.precision == MAP_PREC_BF16,
-                                    h->n_sm, s);
+                                    h->n_sm, s, pose);
         });
+    if (!rc && pose) {
+        rc = phase(h, MAP_PH_FIELD_BWD, 1, s, [&] { launch_pose_reduce(h->dc, n_rays, b, h->pose_g, s); });
+        if (!rc) h->pose_valid = true;
+    }
     if (rc) return rc;
     h->last_rays = n_rays;
     if (!(flags & MAP_STEP_NO_UPDATE)) {
@@ -474,6 +508,40 @@ int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float
 }
 
 const float* map_loss_device(map_handle h) { return h ? h->bufs.loss : nullptr; }
+
+int map_get_pose_grads(map_handle h, float* dst, uint32_t n_kf, int mem_kind, void* stream) {
+    if (!h) return MAP_EINVAL;
+    if (!dst || n_kf > h->kfs.size()) return fail(h, MAP_EINVAL, "n_kf exceeds the number of keyframes");
+    if (!h->pose_valid) return fail(h, MAP_EINVAL, "no pose gradient: run map_step with MAP_STEP_POSE_GRAD");
+    if (n_kf == 0) return MAP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaMemcpyKind kind = mem_kind == MAP_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    // slot rows of 8 floats -> rows of 6
+    NM_CUDA(h, cudaMemcpy2DAsync(dst, 6 * sizeof(float), h->pose_g, 8 * sizeof(float), 6 * sizeof(float), n_kf,
+                                 kind, s));
+    if (mem_kind != MAP_MEM_DEVICE) NM_CUDA(h, cudaStreamSynchronize(s));
+    return MAP_OK;
+}
+
+int map_get_keyframe_ids(map_handle h, uint32_t* ids, uint32_t n) {
+    if (!h) return MAP_EINVAL;
+    const uint32_t k = (uint32_t)h->kfs.size();
+    if (ids)
+        for (uint32_t i = 0; i < std::min(n, k); ++i) ids[i] = h->kfs[i].id;
+    return (int)k;
+}
+
+int map_set_keyframe_pose(map_handle h, uint32_t kf_id, const float c2w[12], void* stream) {
+    if (!h) return MAP_EINVAL;
+    if (!c2w) return fail(h, MAP_EINVAL, "null pose");
+    for (size_t i = 0; i < h->kfs.size(); ++i) {
+        if (h->kfs[i].id != kf_id) continue;
+        std::memcpy(h->kf_desc[i].c2w, c2w, sizeof(h->kf_desc[i].c2w));
+        launch_set_kf_desc(h->d_kfs, (uint32_t)i, h->kf_desc[i], (cudaStream_t)stream);
+        return check_launch(h, "keyframe pose");
+    }
+    return fail(h, MAP_EINVAL, "unknown kf_id");
+}
 
 int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, uint32_t H, float* out_rgb,
                float* out_depth, float* out_acc, int mem_kind, void* stream) {

@@ -194,6 +194,54 @@ __device__ __forceinline__ void sh16(float x, float y, float z, float* out) {
     out[15] = -c3a * x * (xx - 3.f * yy);
 }
 
+// J^T g for the Jacobian J [16 x 3] of sh16 with respect to the direction (each
+// basis function differentiated as the polynomial in x, y, z that sh16 evaluates).
+__device__ __forceinline__ float3 sh16_vjp(float x, float y, float z, const float* g) {
+    const float kPi = 3.14159265358979323846f;
+    const float c1 = sqrtf(3.f / (4.f * kPi));
+    const float c2a = 0.5f * sqrtf(15.f / kPi);
+    const float c2b = 0.25f * sqrtf(5.f / kPi);
+    const float c2c = 0.25f * sqrtf(15.f / kPi);
+    const float c3a = 0.25f * sqrtf(35.f / (2.f * kPi));
+    const float c3b = 0.5f * sqrtf(105.f / kPi);
+    const float c3c = 0.25f * sqrtf(21.f / (2.f * kPi));
+    const float c3d = 0.25f * sqrtf(7.f / kPi);
+    const float c3e = 0.25f * sqrtf(105.f / kPi);
+    const float xx = x * x, yy = y * y, zz = z * z;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    // band 1: -c1 y, c1 z, -c1 x
+    gy -= c1 * g[1];
+    gz += c1 * g[2];
+    gx -= c1 * g[3];
+    // band 2
+    gx += c2a * y * g[4];
+    gy += c2a * x * g[4];
+    gy -= c2a * z * g[5];
+    gz -= c2a * y * g[5];
+    gz += 6.f * c2b * z * g[6];
+    gx -= c2a * z * g[7];
+    gz -= c2a * x * g[7];
+    gx += 2.f * c2c * x * g[8];
+    gy -= 2.f * c2c * y * g[8];
+    // band 3
+    gx -= 6.f * c3a * x * y * g[9];
+    gy -= c3a * (3.f * xx - 3.f * yy) * g[9];
+    gx += c3b * y * z * g[10];
+    gy += c3b * x * z * g[10];
+    gz += c3b * x * y * g[10];
+    gy -= c3c * (5.f * zz - 1.f) * g[11];
+    gz -= 10.f * c3c * y * z * g[11];
+    gz += c3d * (15.f * zz - 3.f) * g[12];
+    gx -= c3c * (5.f * zz - 1.f) * g[13];
+    gz -= 10.f * c3c * x * z * g[13];
+    gx += 2.f * c3e * x * z * g[14];
+    gy -= 2.f * c3e * y * z * g[14];
+    gz += c3e * (xx - yy) * g[14];
+    gx -= c3a * (3.f * xx - 3.f * yy) * g[15];
+    gy += 6.f * c3a * x * y * g[15];
+    return make_float3(gx, gy, gz);
+}
+
 // ----------------------------------------------------------------- error flag
 // Kernels record an out-of-range condition (which they then skip) in a device word
 // the host reads after the step; nothing on the device traps.

@@ -182,6 +182,46 @@ __device__ __forceinline__ void hash_scatter_warp(const DevCfg& c, float2* __res
     }
 }
 
+// dL/dx = sum_l (d f_l / dx) . dL/df_l at grid position x, for the pose gradient:
+// inside a cell of level l (resolution N) the trilinear weight of corner k is
+// w_k = prod_a (b_a ? w_a : 1 - w_a) with w_a = x_a N - c_a, so
+// dw_k/dx_a = N (b_a ? 1 : -1) prod_{a' != a} (b_a' ? w_a' : 1 - w_a'); the table
+// values of the 8 corners are read again.  df: dL/df [kEnc].
+__device__ __forceinline__ float3 hash_grad_x(const DevCfg& c, const float2* __restrict__ tables, float3 x,
+                                              const float* df) {
+    const uint32_t Tmask = c.T - 1;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll 1
+    for (int l = 0; l < kEnc / 2; ++l) {
+        if (l >= (int)c.L) break;
+        const uint32_t N = c.res[l];
+        const bool dense = (c.dense_mask >> l) & 1u;
+        uint32_t cx, cy, cz;
+        float wx, wy, wz;
+        level_cell(x.x, N, cx, wx);
+        level_cell(x.y, N, cy, wy);
+        level_cell(x.z, N, cz, wz);
+        const float2* tab = tables + (size_t)l * c.T;
+        const float g0 = df[2 * l], g1 = df[2 * l + 1];
+        float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int bx = k & 1, by = (k >> 1) & 1, bz = (k >> 2) & 1;
+            const uint32_t slot = vertex_slot(cx + bx, cy + by, cz + bz, N, dense, Tmask);
+            const float2 v = __ldg(tab + slot);
+            const float e = v.x * g0 + v.y * g1;                    // corner value . dL/df_l
+            const float fx = bx ? wx : 1.f - wx, fy = by ? wy : 1.f - wy, fz = bz ? wz : 1.f - wz;
+            ax += (bx ? e : -e) * fy * fz;
+            ay += (by ? e : -e) * fx * fz;
+            az += (bz ? e : -e) * fx * fy;
+        }
+        gx += (float)N * ax;
+        gy += (float)N * ay;
+        gz += (float)N * az;
+    }
+    return make_float3(gx, gy, gz);
+}
+
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
 
 }  // namespace nm

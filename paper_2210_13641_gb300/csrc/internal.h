@@ -18,8 +18,9 @@ struct KfDesc {
     const float4* texels;
 };
 
-// Ray batch, structure of arrays: 11 planes of `cap` floats.
-enum RayPlane { kOx = 0, kOy, kOz, kDx, kDy, kDz, kIr, kIg, kIb, kD, kV, kRayPlanes };
+// Ray batch, structure of arrays: 12 planes of `cap` floats (kKf holds the ray's
+// keyframe slot as the bits of a uint32).
+enum RayPlane { kOx = 0, kOy, kOz, kDx, kDy, kDz, kIr, kIg, kIb, kD, kV, kKf, kRayPlanes };
 
 constexpr uint32_t kCompositeMaxBlocks = 4096;
 
@@ -37,6 +38,7 @@ struct StepBufs {
     float* ray_out;         // [5][cap_rays] I*r, I*g, I*b, D*, acc
     float* loss;            // [0] batch loss, [1] [2] largest seeds (FP32 bits), [3] block counter
     float* partials;        // [kCompositeMaxBlocks][4] per-block sums of the compositing kernel
+    float4* pose_s;         // [cap_samples][2] per-sample pose terms (dL/dp, dL/dd via SH); lazily
     uint32_t* err;          // [1]
     uint64_t cap_samples;
 };
@@ -59,14 +61,19 @@ void launch_scan_counts(const uint32_t* counts, uint32_t n, uint32_t* offsets, u
 // k_field_fp32.cu
 void launch_field_fwd_fp32(const DevCfg& c, const float* params, uint32_t n_rays,
                            const StepBufs& b, bool store_feat, int n_sm, cudaStream_t s);
+// pose: also write the per-sample pose terms into b.pose_s (joint pose refinement).
 void launch_field_bwd_fp32(const DevCfg& c, const float* params, float* grads, uint32_t n_rays,
-                           const StepBufs& b, int n_sm, cudaStream_t s);
+                           const StepBufs& b, int n_sm, cudaStream_t s, bool pose = false);
 
 // k_field_tc.cu (FP16 / BF16 tensor-core MLP)
 void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b,
                          bool store_feat, bool bf16, int n_sm, cudaStream_t s);
 void launch_field_bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t n_rays,
-                         const StepBufs& b, bool bf16, int n_sm, cudaStream_t s);
+                         const StepBufs& b, bool bf16, int n_sm, cudaStream_t s, bool pose = false);
+
+// k_pose.cu: per-ray sums of the per-sample pose terms, accumulated per keyframe slot
+// into pose_g[slot][8] = (dL/drho, dL/dphi, 0, 0); pose_g must be zeroed first.
+void launch_pose_reduce(const DevCfg& c, uint32_t n_rays, const StepBufs& b, float* pose_g, cudaStream_t s);
 
 // k_composite.cu
 void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const StepBufs& b,

@@ -171,6 +171,9 @@ __device__ __forceinline__ void tile_outer(const float* __restrict__ act, int a_
     }
 }
 
+// kPose: also writes, per sample, dL/dp (world position) and the view-direction
+// gradient through the SH encoding into pose_s[2 i], pose_s[2 i + 1].
+template <bool kPose>
 __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float* __restrict__ params,
                                                           float* __restrict__ grads,
                                                           const float* __restrict__ rays, uint32_t cap,
@@ -178,7 +181,8 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
                                                           const uint32_t* __restrict__ ray_id,
                                                           const float* __restrict__ ts,
                                                           const float* __restrict__ feat,
-                                                          const float4* __restrict__ dsig_rgb) {
+                                                          const float4* __restrict__ dsig_rgb,
+                                                          float4* __restrict__ pose_s) {
     extern __shared__ float smem_raw[];
     SmemBwd& s = *reinterpret_cast<SmemBwd*>(smem_raw);
     const float* mlp = params + (size_t)c.L * c.T * 2;
@@ -200,11 +204,11 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
         const uint32_t i = tile * kTile + threadIdx.x;
         const bool valid = i < n;
         float3 x = make_float3(0.f, 0.f, 0.f);
+        float3 d = make_float3(0.f, 0.f, 0.f);
         float dsig = 0.f, sigma = 0.f;
         bool sig_grad_off = false;
         if (valid) {
             // ---- recompute the forward pass into this sample's row
-            float3 d;
             x = sample_pos(c, rays, cap, ray_id[i], ts[i], d);
             float f[kEnc];
             const float4* fi = reinterpret_cast<const float4*>(feat + (size_t)i * kEnc);
@@ -318,6 +322,20 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
                 for (int m = 0; m < kGeo; ++m) dy[m] += W3[nn * 32 + m] * a;
             }
             if (!sig_grad_off) dy[0] += dsig * sigma;
+            if (kPose) {
+                // the SH inputs' gradient (W3^T dA3)[16:32] -> the view-direction gradient
+                float dsh[kSH];
+#pragma unroll
+                for (int m = 0; m < kSH; ++m) dsh[m] = 0.f;
+#pragma unroll 4
+                for (int nn = 0; nn < kHid; ++nn) {
+                    const float a = row[kRh3 + nn];
+#pragma unroll
+                    for (int m = 0; m < kSH; ++m) dsh[m] += W3[nn * 32 + kGeo + m] * a;
+                }
+                const float3 gd = sh16_vjp(d.x, d.y, d.z, dsh);
+                if (valid) pose_s[2 * (size_t)i + 1] = make_float4(gd.x, gd.y, gd.z, 0.f);
+            }
 #pragma unroll
             for (int m = 0; m < kGeo; ++m) row[kRx3 + m] = dy[m];
         }
@@ -353,6 +371,10 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
                 }
             }
             hash_scatter_warp(c, gtables, x, df, valid);
+            if (kPose && valid) {
+                const float3 gx = hash_grad_x(c, reinterpret_cast<const float2*>(params), x, df);
+                pose_s[2 * (size_t)i] = make_float4(gx.x * c.inv_size, gx.y * c.inv_size, gx.z * c.inv_size, 0.f);
+            }
         }
         __syncthreads();
     }
@@ -364,15 +386,21 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
 }
 
 void launch_field_bwd_fp32(const DevCfg& c, const float* params, float* grads, uint32_t n_rays,
-                           const StepBufs& b, int n_sm, cudaStream_t st) {
+                           const StepBufs& b, int n_sm, cudaStream_t st, bool pose) {
     const size_t smem = sizeof(SmemBwd);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_field_bwd_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_field_bwd_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_field_bwd_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_field_bwd_fp32<<<n_sm, kTile, smem, st>>>(c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays,
-                                                b.ray_id, b.t, b.feat, b.dsig_rgb);
+    if (pose)
+        k_field_bwd_fp32<true><<<n_sm, kTile, smem, st>>>(c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays,
+                                                          b.ray_id, b.t, b.feat, b.dsig_rgb, b.pose_s);
+    else
+        k_field_bwd_fp32<false><<<n_sm, kTile, smem, st>>>(c, params, grads, b.rays, b.cap_rays,
+                                                           b.offsets + n_rays, b.ray_id, b.t, b.feat, b.dsig_rgb,
+                                                           nullptr);
 }
 
 }  // namespace nm

@@ -399,7 +399,10 @@ __device__ __forceinline__ uint32_t df_offset(int r, int q) { return (uint32_t)(
 
 }  // namespace
 
-template <bool BF16>
+// kPose: also writes, per sample, dL/dp (world position; IO group) and the
+// view-direction gradient through the SH encoding (MLP group) into pose_s[2 i],
+// pose_s[2 i + 1].
+template <bool BF16, bool kPose>
 __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* __restrict__ params,
                                                          float* __restrict__ grads, const float* __restrict__ rays,
                                                          uint32_t cap, const uint32_t* __restrict__ n_total,
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                                                          const float4* __restrict__ sig_rgb,
                                                          const float4* __restrict__ dsig_rgb, float feat_scale,
                                                          const float* __restrict__ seed_max,
-                                                         uint32_t* __restrict__ err) {
+                                                         float4* __restrict__ pose_s, uint32_t* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tslot;
@@ -530,6 +533,15 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 mma_commit(&bar);
             }
             wait_mma(&bar, phase, timed_out);
+            if (kPose) {
+                // the SH inputs' gradient (columns 16..31, colour scale) -> view direction
+                ld_cols<16>(trow, 16, v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] *= inv_Sc;
+                const float3 gd = sh16_vjp(rd.x, rd.y, rd.z, v);
+                const uint32_t i = (blockIdx.x + k * gridDim.x) * 128 + r;
+                if (valid) pose_s[2 * (size_t)i + 1] = make_float4(gd.x, gd.y, gd.z, 0.f);
+            }
             ld_cols<16>(trow, 0, v);
 #pragma unroll
             for (int q = 0; q < 16; ++q) v[q] *= c_to_d;                // colour scale -> density scale
@@ -597,11 +609,13 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
         float2* gtables = reinterpret_cast<float2*>(grads);
         float3 x_cur = make_float3(0.f, 0.f, 0.f), x_next = x_cur;
         bool valid_cur = false, valid_next = false;
+        uint32_t i_cur = 0, i_next = 0;
         uint4 f_next[4];
         float4 rd_next, rz_next;
         // inputs of this block's k-th tile for row r, into registers
         auto load = [&](uint32_t k) {
             const uint32_t i = (blockIdx.x + k * gridDim.x) * 128 + r;
+            i_next = i;
             valid_next = i < n;
             float3 d = make_float3(0.f, 0.f, 0.f);
             x_next = make_float3(0.f, 0.f, 0.f);
@@ -626,6 +640,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
             sRow[2 * r + 1] = rz_next;
             x_cur = x_next;
             valid_cur = valid_next;
+            i_cur = i_next;
             fence_proxy_async();                      // X0 is read by the tensor core
             nb_arrive(kBarIn, 256);
         };
@@ -638,6 +653,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
             nb_sync(kBarDfReady, 256);
             const float3 x_done = x_cur;
             const bool valid_done = valid_cur;
+            const uint32_t i_done = i_cur;
             float v[32];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -650,6 +666,11 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
             if (k + 1 < n_mine) publish();            // next tile's inputs; the MLP group starts on it
             if (k + 1 < n_mine) nb_arrive(kBarDfFree, 256);
             hash_scatter_warp(c, gtables, x_done, v, valid_done);
+            if (kPose && valid_done) {
+                const float3 gx = hash_grad_x(c, reinterpret_cast<const float2*>(params), x_done, v);
+                pose_s[2 * (size_t)i_done] =
+                    make_float4(gx.x * c.inv_size, gx.y * c.inv_size, gx.z * c.inv_size, 0.f);
+            }
         }
         __syncthreads_or(false);                      // pairs with the MLP group's flush barrier
     }
@@ -676,18 +697,18 @@ static void fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const 
                                                           fs, b.err);
 }
 
-template <bool BF16>
+template <bool BF16, bool kPose>
 static void bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t n_rays, const StepBufs& b, int n_sm,
                    cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_field_bwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem);
+        cudaFuncSetAttribute(k_field_bwd_tc<BF16, kPose>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem);
         attr = true;
     }
     const float fs = BF16 ? 1.f : 256.f;
-    k_field_bwd_tc<BF16><<<n_sm * 2, 256, kBwdSmem, s>>>(c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays,
-                                                          b.ray_id, b.t, reinterpret_cast<const uint4*>(b.feat),
-                                                          b.sig_rgb, b.dsig_rgb, fs, b.loss, b.err);
+    k_field_bwd_tc<BF16, kPose><<<n_sm * 2, 256, kBwdSmem, s>>>(
+        c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays, b.ray_id, b.t, reinterpret_cast<const uint4*>(b.feat),
+        b.sig_rgb, b.dsig_rgb, fs, b.loss, kPose ? b.pose_s : nullptr, b.err);
 }
 
 void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b, bool store_feat,
@@ -697,9 +718,14 @@ void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, 
 }
 
 void launch_field_bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t n_rays, const StepBufs& b,
-                         bool bf16, int n_sm, cudaStream_t s) {
-    if (bf16) bwd_tc<true>(c, params, grads, n_rays, b, n_sm, s);
-    else bwd_tc<false>(c, params, grads, n_rays, b, n_sm, s);
+                         bool bf16, int n_sm, cudaStream_t s, bool pose) {
+    if (pose) {
+        if (bf16) bwd_tc<true, true>(c, params, grads, n_rays, b, n_sm, s);
+        else bwd_tc<false, true>(c, params, grads, n_rays, b, n_sm, s);
+    } else {
+        if (bf16) bwd_tc<true, false>(c, params, grads, n_rays, b, n_sm, s);
+        else bwd_tc<false, false>(c, params, grads, n_rays, b, n_sm, s);
+    }
 }
 
 }  // namespace nm

@@ -59,7 +59,7 @@ __device__ __forceinline__ void cast_ray(const float* c2w, const float* K, uint3
 }
 
 __device__ __forceinline__ void store_ray(float* rays, uint32_t cap, uint32_t r, float3 o,
-                                          float3 d, float4 t0, float V) {
+                                          float3 d, float4 t0, float V, uint32_t kf) {
     rays[kOx * cap + r] = o.x;
     rays[kOy * cap + r] = o.y;
     rays[kOz * cap + r] = o.z;
@@ -71,6 +71,7 @@ __device__ __forceinline__ void store_ray(float* rays, uint32_t cap, uint32_t r,
     rays[kIb * cap + r] = t0.z;
     rays[kD * cap + r] = t0.w;
     rays[kV * cap + r] = V;
+    rays[kKf * cap + r] = __uint_as_float(kf);
 }
 
 // Uniform draw with replacement over (keyframe, pixel): keyframe = r0 mod n_kf,
@@ -81,14 +82,15 @@ __global__ void k_ray_gen(const KfDesc* __restrict__ kfs, uint32_t n_kf, uint64_
     if (r >= n_rays) return;
     const uint64_t r0 = counter_rand(seed, step, r, 0);
     const uint64_t r1 = counter_rand(seed, step, r, 1);
-    const KfDesc& kf = kfs[r0 % n_kf];
+    const uint32_t slot = (uint32_t)(r0 % n_kf);
+    const KfDesc& kf = kfs[slot];
     const uint64_t pix = r1 % ((uint64_t)kf.W * kf.H);
     const uint32_t u = (uint32_t)(pix % kf.W), v = (uint32_t)(pix / kf.W);
     float3 o, d;
     cast_ray(kf.c2w, kf.K, u, v, o, d);
     const float4 t0 = __ldg(kf.texels + 2 * pix);
     const float4 t1 = __ldg(kf.texels + 2 * pix + 1);
-    store_ray(rays, cap, r, o, d, t0, t1.x);
+    store_ray(rays, cap, r, o, d, t0, t1.x, slot);
 }
 
 void launch_ray_gen(const KfDesc* kfs, uint32_t n_kf, uint64_t seed, uint64_t step,
@@ -110,7 +112,7 @@ __global__ void k_ray_gen_view(ViewCam cam, uint32_t W, uint32_t p0, uint32_t cn
     const uint32_t pix = p0 + r;
     float3 o, d;
     cast_ray(cam.c2w, cam.K, pix % W, pix / W, o, d);
-    store_ray(rays, cap, r, o, d, make_float4(0.f, 0.f, 0.f, 0.f), 1.f);
+    store_ray(rays, cap, r, o, d, make_float4(0.f, 0.f, 0.f, 0.f), 1.f, 0u);
 }
 
 void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t p0, uint32_t cnt,
