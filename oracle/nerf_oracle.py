@@ -769,3 +769,39 @@ def hash_encode_f64(cfg, level_res, tables, x):
             wk = np.prod(np.where(bk[None, :] == 1, w, 1.0 - w), axis=1)
             feat[:, l * F:(l + 1) * F] += wk[:, None] * tab[l, vertex_index(c + bk[None, :], N, T)]
     return feat
+
+
+# ------------------------------------------------------------------ depth covariances
+# The per-pixel depth variances Sigma_D that weight the depth loss come from the
+# tracking frontend's dense bundle adjustment: its Hessian has the cameras/depths
+# arrow structure H = [[C, E], [E^T, P]] (Sec. 3.1, Eq. hessian: C the camera block,
+# P diagonal with one entry per pixel inverse depth, E the coupling), and the
+# marginal covariances follow from the Schur complement (Sec. 3.1, Eq. cov):
+#   H_T = C - E P^-1 E^T = L L^T,  Sigma_T = (L L^T)^-1,
+#   Sigma_d = P^-1 + P^-T E^T Sigma_T E P^-1   (its diagonal: one variance per pixel).
+
+def arrow_dense_E(c: int, blk: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """E [c, p] from the block-sparse form: column q holds e[q, b] at rows
+    6 blk[q, b] .. 6 blk[q, b] + 5 (blocks with blk < 0 are unused)."""
+    p, B = blk.shape
+    E = np.zeros((c, p))
+    for q in range(p):
+        for b in range(B):
+            k = int(blk[q, b])
+            if k >= 0:
+                E[6 * k:6 * k + 6, q] += e[q, b]
+    return E
+
+
+def marginal_covariances(C: np.ndarray, P: np.ndarray, blk: np.ndarray, e: np.ndarray):
+    """Eq. (cov) in FP64: returns Sigma_T [c, c] and the per-pixel marginal variances
+    diag(Sigma_d) [p]."""
+    c = C.shape[0]
+    E = arrow_dense_E(c, blk, e)
+    EP = E / P[None, :]                                   # E P^-1
+    HT = C - EP @ E.T                                     # reduced camera matrix
+    L = np.linalg.cholesky(HT)
+    Linv = np.linalg.inv(L)
+    ST = Linv.T @ Linv                                    # (L L^T)^-1
+    Sd = 1.0 / P + np.einsum("ip,ij,jp->p", EP, ST, EP)
+    return ST, Sd
