@@ -264,6 +264,40 @@ def sigma_d_ablation(precision="fp16", steps=3000, outlier_frac=0.2, seeds=(0, 1
     return out
 
 
+# ----------------------------------------------------------------- depth covariances
+
+def covariance_benchmark(n_kf=20, px=80 * 60, links=3, reps=5):
+    """Marginal covariances of a dense-BA arrow Hessian the size of a tracking window
+    (n_kf keyframes of px inverse depths at 1/8 resolution, each linked to `links`
+    others): wall time of map_marginal_covariances with device-resident FP64 inputs."""
+    import numpy as np
+    import torch
+    from synth.arrow import arrow_hessian
+    from paper_2210_13641_gb300 import binding as _b
+    h = arrow_hessian(n_kf, px, links, seed=0)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(h[k])).cuda() for k in ("C", "P", "blk", "e")}
+    ST = torch.empty((h["c"], h["c"]), dtype=torch.float64, device="cuda")
+    Sd = torch.empty(h["p"], dtype=torch.float64, device="cuda")
+    lib = _b.load()
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def run():
+        rc = lib.map_marginal_covariances(dev["C"].data_ptr(), h["c"], dev["P"].data_ptr(), h["p"],
+                                          dev["blk"].data_ptr(), dev["e"].data_ptr(), h["B"], ST.data_ptr(),
+                                          Sd.data_ptr(), _b.MAP_MEM_DEVICE, stream)
+        if rc != 0:
+            raise _b.MapError(rc, lib.map_last_error(None).decode())
+
+    run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        run()
+    ms = (time.perf_counter() - t0) / reps * 1e3
+    return {"keyframes": n_kf, "pixels": h["p"], "links": links, "camera_dim": h["c"], "ms": ms,
+            "pixels_per_s": h["p"] / (ms / 1e3)}
+
+
 # ----------------------------------------------------------------- large map
 
 def large_map_benchmark(n_kf=2000, W=1200, H=680, rays=1 << 20, steps=5, warmup=2, seed=0,
@@ -636,6 +670,7 @@ def main():
     if not args.no_large_map and rank == 0:
         large = large_map_benchmark(n_kf=args.large_map_keyframes)
     ablation = sigma_d_ablation(args.precision) if args.ablation and rank == 0 else None
+    cov = covariance_benchmark() if rank == 0 and not args.no_large_map else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -655,6 +690,8 @@ def main():
             line["large_map"] = large
         if ablation:
             line["sigma_d_ablation"] = ablation
+        if cov:
+            line["depth_covariance"] = cov
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

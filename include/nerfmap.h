@@ -223,6 +223,26 @@ int map_get_grads(map_handle h, float* dst, size_t n, int mem_kind, void* stream
  * without a preceding POSE_GRAD step.
  */
 int map_get_pose_grads(map_handle h, float* dst, uint32_t n_kf, int mem_kind, void* stream);
+/*
+ * map_marginal_covariances - the per-pixel depth variances that weight the depth
+ * loss, from the tracking frontend's dense bundle adjustment (Sec. 3.1, Eq. cov):
+ * the BA Hessian has the cameras/depths arrow structure H = [[C, E], [E^T, P]]
+ * (Eq. hessian); then H_T = C - E P^-1 E^T = L L^T, Sigma_T = (L L^T)^-1 and
+ * Sigma_d = diag(P^-1 + P^-T E^T Sigma_T E P^-1).  Stateless (no map handle); FP64.
+ * C: c x c row-major (its lower triangle is read), c = 6 x keyframes, 6..144.
+ * P: p positive diagonal entries (one per pixel inverse depth).  E block-sparse:
+ * blk [p][B] int32 pose index per block (< c/6, or -1 = unused), e [p][B][6] the
+ * rows 6 blk .. 6 blk + 5 of column q of E; 1 <= B <= 8.  Outputs: sigma_T c x c
+ * row-major, sigma_d [p].  All arrays in mem_kind memory; the call waits for the
+ * stream.  Errors: MAP_EINVAL (sizes, a non-positive P entry, a reduced camera
+ * matrix that is not positive definite; message in map_last_error(NULL)),
+ * MAP_ENOMEM, MAP_ECUDA.  The paper computes these in its tracking frontend; here
+ * they take synthetic Hessians.
+ */
+int map_marginal_covariances(const double* C, uint32_t c, const double* P, uint32_t p,
+                             const int32_t* blk, const double* e, uint32_t B, double* sigma_T,
+                             double* sigma_d, int mem_kind, void* stream);
+
 /* The kf_id of each keyframe slot: ids[s] for s < min(n, number of keyframes);
  * returns the number of keyframes (host memory). */
 int map_get_keyframe_ids(map_handle h, uint32_t* ids, uint32_t n);

@@ -98,6 +98,9 @@ _SIGS = {
     "map_get_pose_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int,
                                           ctypes.c_void_p]),
     "map_get_keyframe_ids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]),
+    "map_marginal_covariances": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "map_set_keyframe_pose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "map_get_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                     ctypes.c_int, ctypes.c_void_p]),
@@ -572,3 +575,21 @@ class MapServer:
         st = ServerStats()
         self.lib.map_server_get_stats(self.h, ctypes.byref(st))
         return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+
+def marginal_covariances(C, P, blk, e, stream=None):
+    """Sigma_T [c, c] and the per-pixel depth variances Sigma_d [p] of a dense-BA arrow
+    Hessian (map_marginal_covariances).  Host numpy inputs (FP64; blk int32)."""
+    lib = load()
+    C = np.ascontiguousarray(C, np.float64)
+    P = np.ascontiguousarray(P, np.float64)
+    blk = np.ascontiguousarray(blk, np.int32)
+    e = np.ascontiguousarray(e, np.float64)
+    c, p, B = C.shape[0], P.shape[0], blk.shape[1]
+    ST = np.zeros((c, c))
+    Sd = np.zeros(p)
+    rc = lib.map_marginal_covariances(C.ctypes.data, c, P.ctypes.data, p, blk.ctypes.data, e.ctypes.data, B,
+                                      ST.ctypes.data, Sd.ctypes.data, MAP_MEM_HOST, _stream(stream))
+    if rc != 0:
+        raise MapError(rc, lib.map_last_error(None).decode())
+    return ST, Sd

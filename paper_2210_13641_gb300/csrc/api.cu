@@ -13,6 +13,7 @@
 using namespace nm;
 
 const char* nm_noalloc_last_error();
+const char* nm_cov_last_error();
 
 namespace {
 
@@ -768,7 +769,9 @@ size_t map_abi_config_size(void) { return sizeof(map_config); }
 const char* map_last_error(map_handle h) {
     if (h) return h->err.c_str();
     const char* m = nm_noalloc_last_error();
-    return m[0] ? m : g_create_error.c_str();
+    if (m[0]) return m;
+    const char* cv = nm_cov_last_error();
+    return cv[0] ? cv : g_create_error.c_str();
 }
 
 }  // extern "C"

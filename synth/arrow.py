@@ -22,7 +22,8 @@ def arrow_hessian(n_kf: int = 6, px_per_kf: int = 48, links: int = 2, seed: int 
     unused), e [p, B, 6], c = 6 n_kf, p = n_kf * px_per_kf, B = links + 1).  FP64."""
     rng = np.random.default_rng(seed)
     c = 6 * n_kf
-    p = n_kf * px_per_kf
+    n = px_per_kf
+    p = n_kf * n
     B = links + 1
     C = np.zeros((c, c))
     P = np.zeros(p)
@@ -30,22 +31,20 @@ def arrow_hessian(n_kf: int = 6, px_per_kf: int = 48, links: int = 2, seed: int 
     e = np.zeros((p, B, 6))
     for i in range(n_kf):
         others = rng.choice([k for k in range(n_kf) if k != i], size=min(links, n_kf - 1), replace=False)
-        for u in range(px_per_kf):
-            q = i * px_per_kf + u
-            blk[q, 0] = i
-            for b, j in enumerate(others):
-                blk[q, b + 1] = j
-            for j_idx, j in enumerate(others):
-                Ji = rng.normal(size=(2, 6))
-                Jj = rng.normal(size=(2, 6))
-                Jd = rng.normal(size=(2, 1)) * 3.0
-                Wd = np.diag(rng.uniform(0.2, 2.0, size=2))
-                for (a, Ja) in ((i, Ji), (j, Jj)):
-                    for (bb, Jb) in ((i, Ji), (j, Jj)):
-                        C[6 * a:6 * a + 6, 6 * bb:6 * bb + 6] += Ja.T @ Wd @ Jb
-                P[q] += float((Jd.T @ Wd @ Jd)[0, 0])
-                e[q, 0] += (Ji.T @ Wd @ Jd)[:, 0]
-                e[q, j_idx + 1] += (Jj.T @ Wd @ Jd)[:, 0]
+        rows = slice(i * n, (i + 1) * n)
+        blk[rows, 0] = i
+        for jj, j in enumerate(others):
+            blk[rows, jj + 1] = j
+            Ji = rng.normal(size=(n, 2, 6))
+            Jj = rng.normal(size=(n, 2, 6))
+            Jd = rng.normal(size=(n, 2)) * 3.0
+            w = rng.uniform(0.2, 2.0, size=(n, 2))             # diagonal flow weights
+            for (a, Ja) in ((i, Ji), (j, Jj)):
+                for (bb, Jb) in ((i, Ji), (j, Jj)):
+                    C[6 * a:6 * a + 6, 6 * bb:6 * bb + 6] += np.einsum("nra,nr,nrb->ab", Ja, w, Jb)
+            P[rows] += np.einsum("nr,nr,nr->n", Jd, w, Jd)
+            e[rows, 0] += np.einsum("nra,nr,nr->na", Ji, w, Jd)
+            e[rows, jj + 1] += np.einsum("nra,nr,nr->na", Jj, w, Jd)
     C[:6, :6] += gauge_prior * np.eye(6)
     return dict(C=C, P=P, blk=blk, e=e, c=c, p=p, B=B)
 
