@@ -454,10 +454,10 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 # kernel sources are the ones captured: the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
-    "sha256": "e3262e8a02adca290a073d6bf82e296bed7c417626b09edd788dc3d302d8efe0",
+    "sha256": "6057ea404e3069d1f0d3e85a391a96ab192d86dd448012cf137d05b006064259",
     "samples": 15869619,
-    "field_fwd": 311756544 + 1244720640,
-    "field_bwd": 1720641280 + 206029568,
+    "field_fwd": 312187904 + 1244495360,
+    "field_bwd": 1720803584 + 207130880,
 }
 
 

@@ -243,6 +243,24 @@ int map_marginal_covariances(const double* C, uint32_t c, const double* P, uint3
                              const int32_t* blk, const double* e, uint32_t B, double* sigma_T,
                              double* sigma_d, int mem_kind, void* stream);
 
+/*
+ * Keyframe streaming (the paper's memory mitigation, Sec. 6: inactive parts of the
+ * map are streamed to the CPU and only a window around the region of interest is
+ * kept on the GPU).  map_evict_keyframe copies a keyframe's images to pinned host
+ * memory and frees its device memory; from then on map_step draws rays only from
+ * the device-resident keyframes, the k-th of them in slot order taking the place of
+ * keyframe k of the draw (the keyframe slots and ids are unchanged).
+ * map_restore_keyframe brings the images back (bit-identical) and makes the
+ * keyframe drawable again; map_add_keyframe with the id of a streamed-out keyframe
+ * replaces it with the new images.  Both wait for the stream.  Already evicted /
+ * resident: no-op.  MAP_EINVAL for an unknown kf_id; map_step returns MAP_ENOKF
+ * while every keyframe is streamed out.  map_keyframe_resident: 1 resident, 0
+ * streamed out, MAP_EINVAL unknown.
+ */
+int map_evict_keyframe(map_handle h, uint32_t kf_id, void* stream);
+int map_restore_keyframe(map_handle h, uint32_t kf_id, void* stream);
+int map_keyframe_resident(map_handle h, uint32_t kf_id);
+
 /* The kf_id of each keyframe slot: ids[s] for s < min(n, number of keyframes);
  * returns the number of keyframes (host memory). */
 int map_get_keyframe_ids(map_handle h, uint32_t* ids, uint32_t n);

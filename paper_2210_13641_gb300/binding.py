@@ -98,6 +98,9 @@ _SIGS = {
     "map_get_pose_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int,
                                           ctypes.c_void_p]),
     "map_get_keyframe_ids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]),
+    "map_evict_keyframe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "map_restore_keyframe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "map_keyframe_resident": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "map_marginal_covariances": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -348,6 +351,17 @@ class NerfMap:
         out = np.zeros((n, 6), np.float32)
         self._check(self.lib.map_get_pose_grads(self.h, out.ctypes.data, n, MAP_MEM_HOST, _stream(stream)))
         return out
+
+    def evict_keyframe(self, kf_id: int, stream=None):
+        self._check(self.lib.map_evict_keyframe(self.h, kf_id, _stream(stream)))
+
+    def restore_keyframe(self, kf_id: int, stream=None):
+        self._check(self.lib.map_restore_keyframe(self.h, kf_id, _stream(stream)))
+
+    def keyframe_resident(self, kf_id: int) -> bool:
+        rc = self.lib.map_keyframe_resident(self.h, kf_id)
+        self._check(min(rc, 0))
+        return rc == 1
 
     def set_pose(self, kf_id: int, c2w, stream=None):
         c2w = np.ascontiguousarray(c2w, np.float32).reshape(12)

@@ -21,8 +21,9 @@ thread_local std::string g_create_error;
 
 struct Keyframe {
     uint32_t id, W, H;
-    float4* texels;
+    float4* texels;          // device texels (nullptr while streamed out)
     size_t bytes;
+    float4* host = nullptr;  // pinned host copy while streamed out
 };
 
 struct PhaseRec {
@@ -56,6 +57,12 @@ struct map_scene {
 
     StepBufs bufs{};
     std::vector<void*> buf_allocs;
+    uint32_t* d_active = nullptr;   // slots of the device-resident keyframes (when some are streamed out)
+    uint32_t d_active_cap = 0;
+    uint32_t* h_active = nullptr;   // pinned staging of that list
+    cudaEvent_t active_ev = nullptr;
+    uint32_t n_active = 0;
+    bool all_active = true;
     float4* pose_s = nullptr;       // per-sample pose terms (allocated on the first POSE_GRAD step)
     uint64_t pose_s_cap = 0;
     float* pose_g = nullptr;        // [pose_g_cap][8] per keyframe slot
@@ -324,11 +331,17 @@ int map_destroy(map_handle h) {
     if (!h) return MAP_EINVAL;
     cudaDeviceSynchronize();
     prof_clear(h);
+    for (auto& kf : h->kfs)
+        if (kf.host) cudaFreeHost(kf.host);
+    if (h->h_active) cudaFreeHost(h->h_active);
+    if (h->active_ev) cudaEventDestroy(h->active_ev);
     for (auto& a : h->allocs) cudaFree(a.first);
     h->allocs.clear();
     delete h;
     return MAP_OK;
 }
+
+static int rebuild_active(map_scene* h, cudaStream_t s);
 
 int map_add_keyframe(map_handle h, uint32_t kf_id, const float c2w[12], const float K[4], uint32_t W,
                      uint32_t H, const float* rgb, const float* depth, const float* depth_var,
@@ -350,6 +363,10 @@ int map_add_keyframe(map_handle h, uint32_t kf_id, const float c2w[12], const fl
     }
     if (idx == h->kfs.size()) h->kfs.push_back(Keyframe{kf_id, W, H, nullptr, 0});
     Keyframe& kf = h->kfs[idx];
+    if (kf.host) {  // a streamed-out keyframe is replaced by the new images
+        cudaFreeHost(kf.host);
+        kf.host = nullptr;
+    }
     kf.W = W;
     kf.H = H;
     if (!kf.texels) {
@@ -361,6 +378,7 @@ int map_add_keyframe(map_handle h, uint32_t kf_id, const float c2w[12], const fl
             if (h->d_kfs)
                 for (size_t i = 0; i < h->kf_desc.size(); ++i)
                     launch_set_kf_desc(h->d_kfs, (uint32_t)i, h->kf_desc[i], s);
+            if (!h->all_active) rebuild_active(h, s);
             return fail(h, rc, h->err);
         }
         kf.bytes = npx * 2 * sizeof(float4);
@@ -408,7 +426,9 @@ int map_add_keyframe(map_handle h, uint32_t kf_id, const float c2w[12], const fl
     } else {
         launch_set_kf_desc(h->d_kfs, (uint32_t)idx, dsc, s);
     }
-    return check_launch(h, "keyframe table");
+    rc = check_launch(h, "keyframe table");
+    if (!rc && !h->all_active) rc = rebuild_active(h, s);  // the new or replaced slot is drawn again
+    return rc;
 }
 
 static int run_forward(map_scene* h, uint32_t n_rays, bool train, cudaStream_t s) {
@@ -427,6 +447,7 @@ int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float
     if (!h) return MAP_EINVAL;
     if (n_rays == 0 || n_rays > (1u << 24)) return fail(h, MAP_EINVAL, "n_rays must be 1..2^24");
     if (h->kfs.empty()) return fail(h, MAP_ENOKF, "no keyframes");
+    if (!h->all_active && h->n_active == 0) return fail(h, MAP_ENOKF, "every keyframe is streamed out");
     cudaStream_t s = (cudaStream_t)stream;
     h->last_stream = s;
     int rc = ensure_step_bufs(h, n_rays);
@@ -462,7 +483,10 @@ int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float
     }
     const StepBufs& b = h->bufs;
     rc = phase(h, MAP_PH_RAYGEN, 1, s,
-               [&] { launch_ray_gen(h->d_kfs, (uint32_t)h->kfs.size(), seed, h->step, n_rays, b, s); });
+               [&] {
+                   launch_ray_gen(h->d_kfs, h->all_active ? nullptr : h->d_active,
+                                  h->all_active ? (uint32_t)h->kfs.size() : h->n_active, seed, h->step, n_rays, b, s);
+               });
     if (!rc) rc = run_forward(h, n_rays, true, s);
     if (!rc) rc = phase(h, MAP_PH_COMPOSITE, 1, s, [&] { launch_composite(h->dc, n_rays, true, b, s); });
     if (!rc)
@@ -509,6 +533,86 @@ int map_step(map_handle h, uint32_t n_rays, uint64_t seed, uint32_t flags, float
 }
 
 const float* map_loss_device(map_handle h) { return h ? h->bufs.loss : nullptr; }
+
+// The list of device-resident keyframe slots the ray draw uses (in slot order);
+// none while every keyframe is resident.  The pinned staging buffer is reused only
+// after the previous upload from it has completed.
+static int rebuild_active(map_scene* h, cudaStream_t s) {
+    std::vector<uint32_t> act;
+    for (size_t i = 0; i < h->kfs.size(); ++i)
+        if (h->kfs[i].texels) act.push_back((uint32_t)i);
+    h->all_active = act.size() == h->kfs.size();
+    h->n_active = (uint32_t)act.size();
+    if (h->all_active || act.empty()) return MAP_OK;
+    if (h->d_active_cap < act.size()) {
+        cudaStreamSynchronize(s);
+        dfree(h, h->d_active);
+        h->d_active = nullptr;
+        if (h->h_active) cudaFreeHost(h->h_active);
+        h->h_active = nullptr;
+        const uint32_t cap = std::max<uint32_t>(64, (uint32_t)h->kfs.size() * 2);
+        int rc = dalloc(h, (void**)&h->d_active, cap * sizeof(uint32_t));
+        if (rc) return rc;
+        NM_CUDA(h, cudaMallocHost((void**)&h->h_active, cap * sizeof(uint32_t)));
+        h->d_active_cap = cap;
+    }
+    if (!h->active_ev) NM_CUDA(h, cudaEventCreateWithFlags(&h->active_ev, cudaEventDisableTiming));
+    NM_CUDA(h, cudaEventSynchronize(h->active_ev));
+    std::memcpy(h->h_active, act.data(), act.size() * sizeof(uint32_t));
+    NM_CUDA(h, cudaMemcpyAsync(h->d_active, h->h_active, act.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    NM_CUDA(h, cudaEventRecord(h->active_ev, s));
+    return MAP_OK;
+}
+
+int map_evict_keyframe(map_handle h, uint32_t kf_id, void* stream) {
+    if (!h) return MAP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (size_t i = 0; i < h->kfs.size(); ++i) {
+        Keyframe& kf = h->kfs[i];
+        if (kf.id != kf_id) continue;
+        if (!kf.texels) return MAP_OK;  // already streamed out
+        NM_CUDA(h, cudaMallocHost((void**)&kf.host, kf.bytes));
+        NM_CUDA(h, cudaMemcpyAsync(kf.host, kf.texels, kf.bytes, cudaMemcpyDeviceToHost, s));
+        NM_CUDA(h, cudaStreamSynchronize(s));  // the copy and every step that read the texels are done
+        dfree(h, kf.texels);
+        kf.texels = nullptr;
+        h->kf_desc[i].texels = nullptr;
+        launch_set_kf_desc(h->d_kfs, (uint32_t)i, h->kf_desc[i], s);
+        int rc = check_launch(h, "keyframe table");
+        if (rc) return rc;
+        return rebuild_active(h, s);
+    }
+    return fail(h, MAP_EINVAL, "unknown kf_id");
+}
+
+int map_restore_keyframe(map_handle h, uint32_t kf_id, void* stream) {
+    if (!h) return MAP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (size_t i = 0; i < h->kfs.size(); ++i) {
+        Keyframe& kf = h->kfs[i];
+        if (kf.id != kf_id) continue;
+        if (kf.texels) return MAP_OK;  // resident
+        int rc = dalloc(h, (void**)&kf.texels, kf.bytes);
+        if (rc) return rc;
+        NM_CUDA(h, cudaMemcpyAsync(kf.texels, kf.host, kf.bytes, cudaMemcpyHostToDevice, s));
+        NM_CUDA(h, cudaStreamSynchronize(s));
+        cudaFreeHost(kf.host);
+        kf.host = nullptr;
+        h->kf_desc[i].texels = kf.texels;
+        launch_set_kf_desc(h->d_kfs, (uint32_t)i, h->kf_desc[i], s);
+        rc = check_launch(h, "keyframe table");
+        if (rc) return rc;
+        return rebuild_active(h, s);
+    }
+    return fail(h, MAP_EINVAL, "unknown kf_id");
+}
+
+int map_keyframe_resident(map_handle h, uint32_t kf_id) {
+    if (!h) return MAP_EINVAL;
+    for (const auto& kf : h->kfs)
+        if (kf.id == kf_id) return kf.texels ? 1 : 0;
+    return fail(h, MAP_EINVAL, "unknown kf_id");
+}
 
 int map_get_pose_grads(map_handle h, float* dst, uint32_t n_kf, int mem_kind, void* stream) {
     if (!h) return MAP_EINVAL;

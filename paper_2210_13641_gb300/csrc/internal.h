@@ -48,7 +48,7 @@ void launch_set_kf_desc(KfDesc* table, uint32_t idx, const KfDesc& d, cudaStream
 void launch_keyframe_texels(const float* rgb, const float* depth, const float* var, uint32_t W,
                             uint32_t H, const float* K, int depth_is_z, float4* texels,
                             cudaStream_t s);
-void launch_ray_gen(const KfDesc* kfs, uint32_t n_kf, uint64_t seed, uint64_t step,
+void launch_ray_gen(const KfDesc* kfs, const uint32_t* active, uint32_t n_kf, uint64_t seed, uint64_t step,
                     uint32_t n_rays, const StepBufs& b, cudaStream_t s);
 void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t p0, uint32_t cnt,
                          const StepBufs& b, cudaStream_t s);

@@ -75,14 +75,17 @@ __device__ __forceinline__ void store_ray(float* rays, uint32_t cap, uint32_t r,
 }
 
 // Uniform draw with replacement over (keyframe, pixel): keyframe = r0 mod n_kf,
-// pixel = r1 mod (W*H), with r0, r1 the two counter draws of the ray.
-__global__ void k_ray_gen(const KfDesc* __restrict__ kfs, uint32_t n_kf, uint64_t seed,
-                          uint64_t step, uint32_t n_rays, float* __restrict__ rays, uint32_t cap) {
+// pixel = r1 mod (W*H), with r0, r1 the two counter draws of the ray.  With an active
+// list (keyframes streamed out to the host are not drawn) the k-th active keyframe is
+// slot active[k]; without one, slot k.
+__global__ void k_ray_gen(const KfDesc* __restrict__ kfs, const uint32_t* __restrict__ active, uint32_t n_kf,
+                          uint64_t seed, uint64_t step, uint32_t n_rays, float* __restrict__ rays, uint32_t cap) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
     const uint64_t r0 = counter_rand(seed, step, r, 0);
     const uint64_t r1 = counter_rand(seed, step, r, 1);
-    const uint32_t slot = (uint32_t)(r0 % n_kf);
+    const uint32_t k = (uint32_t)(r0 % n_kf);
+    const uint32_t slot = active ? active[k] : k;
     const KfDesc& kf = kfs[slot];
     const uint64_t pix = r1 % ((uint64_t)kf.W * kf.H);
     const uint32_t u = (uint32_t)(pix % kf.W), v = (uint32_t)(pix / kf.W);
@@ -93,9 +96,9 @@ __global__ void k_ray_gen(const KfDesc* __restrict__ kfs, uint32_t n_kf, uint64_
     store_ray(rays, cap, r, o, d, t0, t1.x, slot);
 }
 
-void launch_ray_gen(const KfDesc* kfs, uint32_t n_kf, uint64_t seed, uint64_t step,
+void launch_ray_gen(const KfDesc* kfs, const uint32_t* active, uint32_t n_kf, uint64_t seed, uint64_t step,
                     uint32_t n_rays, const StepBufs& b, cudaStream_t s) {
-    k_ray_gen<<<(n_rays + 255) / 256, 256, 0, s>>>(kfs, n_kf, seed, step, n_rays, b.rays,
+    k_ray_gen<<<(n_rays + 255) / 256, 256, 0, s>>>(kfs, active, n_kf, seed, step, n_rays, b.rays,
                                                    b.cap_rays);
 }
 
