@@ -268,3 +268,37 @@ def test_render_in_chunks_matches_oracle_on_sampled_pixels():
     assert np.allclose(rgb.reshape(-1, 3)[pix], ref["I_hat"], rtol=REL, atol=1e-6)
     assert np.allclose(D.ravel()[pix], ref["D_hat"], rtol=REL, atol=1e-6)
     assert np.allclose(acc.ravel()[pix], ref["acc"], rtol=REL, atol=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_maximum_samples_per_ray(prec):
+    """The largest per-ray sample budget (max_samples = 1024): rays with hundreds of
+    samples (many 32-sample chunks in the warp-per-ray march and compositing, many
+    128-sample tiles per ray in the field kernels), some truncated at 1024, a ragged
+    ray count; FP32 to the FP32 tolerance, FP16 to 2e-3 against the oracle with the
+    ReLU branches in FP16."""
+    cfg = synth.config_small(precision=prec, occ_res=0, step=np.float32(4e-4), n_steps=5000,
+                             max_samples=1024)
+    P = synth.random_params(cfg, 9, table_scale=0.05, mlp_std=0.1)
+    kf = synth.c1_keyframe(70, W=20, H=15)
+    m = _map(cfg, P, [kf])
+    n = 301
+    loss = m.step(n, seed=3, no_update=True)
+    ref = oracle.forward_backward(cfg, P, [kf], n, 3, 0, decide_in=None if prec == "fp32" else prec,
+                                  magnitudes=prec == "fp32")
+    counts = np.bincount(ref["ray_id"], minlength=n)
+    assert counts.max() == 1024 and (counts == 1024).sum() > 10 and np.median(counts) > 300
+    if prec == "fp32":
+        _check_step(m, ref, n, loss)
+        _check_grads(m.unpack(m.get_grads()), ref)
+    else:
+        rid, t = m.samples()
+        assert np.array_equal(rid, ref["ray_id"].astype(np.uint32)) and np.array_equal(t, ref["t"])
+        assert loss == pytest.approx(ref["loss"], rel=2e-3)
+        rgb, D, acc = m.ray_outputs(n)
+        assert np.allclose(rgb, ref["I_hat"], rtol=2e-3, atol=2e-3)
+        assert np.allclose(D, ref["D_hat"], rtol=2e-3, atol=2e-3)
+        G = m.unpack(m.get_grads())
+        for k in ("tables", "W1", "W2", "W3", "W4", "W5"):
+            err = np.linalg.norm(G[k] - ref["grads"][k]) / np.linalg.norm(ref["grads"][k])
+            assert err <= 2e-3, (k, err)
