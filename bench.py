@@ -103,6 +103,23 @@ def run_cpu_baseline(sample_rays: int):
                       f"({r['seconds']:.1f} s; Adam over all parameters)"}
 
 
+def max_over_ranks(dist, x, device="cuda"):
+    """The largest value of a per-rank float over all ranks (x itself without a
+    process group): the timing of a multi-GPU run is the slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` independent replicas that each processed
+    units_per_rank units, timed by the slowest rank (weak scaling)."""
+    return units_per_rank * world / seconds
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -548,12 +565,10 @@ def main():
     m.profile(False)
     launches = m.stats().kernel_launches - launches0
     n_samples = m.stats().n_samples
+    ms = max_over_ranks(dist, ms)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = n * args.steps * world / (ms / 1e3)
+    value = replica_throughput(n * args.steps, world, ms / 1e3)
 
     # ---------------- roofline of the dominant kernel (phase times inside the timed region)
     import json as _json
@@ -605,11 +620,8 @@ def main():
         m.step(n, seed=3000 + i, want_loss=True, stream=stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": n * args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e_s = max_over_ranks(dist, e2e_s)
+    e2e = {"value": replica_throughput(n * args.steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": 4}
 
     # ---------------- render Mpx/s (640x480 views, device output buffers)
@@ -656,11 +668,8 @@ def main():
             f1.record(stream)
             torch.cuda.synchronize()
             fms = f0.elapsed_time(f1)
-            if dist:
-                t = torch.tensor([fms], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                fms = float(t.item())
-            forms[prec] = {"value": n * k * world / (fms / 1e3), "ms_per_step": fms / k}
+            fms = max_over_ranks(dist, fms)
+            forms[prec] = {"value": replica_throughput(n * k, world, fms / 1e3), "ms_per_step": fms / k}
             mf.close()
 
     serving = None
