@@ -202,13 +202,10 @@ __global__ void __launch_bounds__(kCompositeWarps * 32) k_composite(
 
 void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const StepBufs& b,
                       cudaStream_t s) {
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (n_sm <= 0) n_sm = 148;
-    }
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (n_sm <= 0) n_sm = 148;
     uint32_t grid = (n_rays + kCompositeWarps - 1) / kCompositeWarps;
     uint32_t cap = (uint32_t)n_sm * 8;  // persistent warps loop over the rays
     if (cap > kCompositeMaxBlocks) cap = kCompositeMaxBlocks;

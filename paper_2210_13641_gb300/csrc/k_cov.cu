@@ -234,14 +234,11 @@ extern "C" int map_marginal_covariances(const double* C, uint32_t c, const doubl
     }
     cudaMemsetAsync(work.p, 0, n_tri * sizeof(double) + 16, s);
     const size_t sh_schur = n_tri * sizeof(double), sh_chol = 2 * n_tri * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_cov_schur, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kCovMaxC * (kCovMaxC + 1) / 2 * sizeof(double)));
-        cudaFuncSetAttribute(k_cov_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kCovMaxC * (kCovMaxC + 1) * sizeof(double)));
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device (cheap next to the kernel)
+    cudaFuncSetAttribute(k_cov_schur, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kCovMaxC * (kCovMaxC + 1) / 2 * sizeof(double)));
+    cudaFuncSetAttribute(k_cov_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kCovMaxC * (kCovMaxC + 1) * sizeof(double)));
     uint32_t grid = (p + 7) / 8;
     if (grid > 152u * 2u) grid = 152u * 2u;
     k_cov_schur<<<grid, 256, sh_schur, s>>>(c, dP, p, dBlk, dE, B, acc, flag);

@@ -120,11 +120,8 @@ __global__ void __launch_bounds__(128) k_field_fwd_fp32(DevCfg c, const float* _
 void launch_field_fwd_fp32(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b,
                            bool store_feat, int n_sm, cudaStream_t st) {
     const size_t smem = sizeof(SmemW);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_field_fwd_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device (cheap next to the kernel)
+    cudaFuncSetAttribute(k_field_fwd_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     (void)n_rays;
     k_field_fwd_fp32<<<n_sm * 8, 128, smem, st>>>(c, params, b.rays, b.cap_rays, b.offsets + n_rays,
                                                  b.ray_id, b.t, b.sig_rgb, store_feat ? b.feat : nullptr);
@@ -388,12 +385,9 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
 void launch_field_bwd_fp32(const DevCfg& c, const float* params, float* grads, uint32_t n_rays,
                            const StepBufs& b, int n_sm, cudaStream_t st, bool pose) {
     const size_t smem = sizeof(SmemBwd);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_field_bwd_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_field_bwd_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device (cheap next to the kernel)
+    cudaFuncSetAttribute(k_field_bwd_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_field_bwd_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (pose)
         k_field_bwd_fp32<true><<<n_sm, kTile, smem, st>>>(c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays,
                                                           b.ray_id, b.t, b.feat, b.dsig_rgb, b.pose_s);

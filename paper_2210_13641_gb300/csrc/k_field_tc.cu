@@ -685,11 +685,8 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
 template <bool BF16>
 static void fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b, bool store_feat,
                    int n_sm, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_field_fwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device (cheap next to the kernel)
+    cudaFuncSetAttribute(k_field_fwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
     const float fs = BF16 ? 1.f : 256.f;
     k_field_fwd_tc<BF16><<<n_sm * 4, 128, kFwdSmem, s>>>(c, params, b.rays, b.cap_rays, b.offsets + n_rays,
                                                           b.ray_id, b.t, b.sig_rgb,
@@ -700,11 +697,8 @@ static void fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const 
 template <bool BF16, bool kPose>
 static void bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t n_rays, const StepBufs& b, int n_sm,
                    cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_field_bwd_tc<BF16, kPose>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem);
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device (cheap next to the kernel)
+    cudaFuncSetAttribute(k_field_bwd_tc<BF16, kPose>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem);
     const float fs = BF16 ? 1.f : 256.f;
     k_field_bwd_tc<BF16, kPose><<<n_sm * 2, 256, kBwdSmem, s>>>(
         c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays, b.ray_id, b.t, reinterpret_cast<const uint4*>(b.feat),
