@@ -91,36 +91,9 @@ __device__ __forceinline__ void hash_encode(const DevCfg& c, const float2* __res
     for (int l0 = 0; l0 < kEnc / 2; l0 += kGatherGroup) encode_group(c, tables, x, l0, f + 2 * l0);
 }
 
-// dL/dtable[l][slot_k] += w_k * dL/df_l for every corner and level (FP32 atomics,
-// one 8-byte vector reduction per corner).
-__device__ __forceinline__ void hash_scatter(const DevCfg& c, float2* __restrict__ gtables,
-                                             float3 x, const float* df) {
-    const uint32_t Tmask = c.T - 1;
-#pragma unroll
-    for (int l = 0; l < kEnc / 2; ++l) {
-        if (l < (int)c.L) {
-            const uint32_t N = c.res[l];
-            const bool dense = (c.dense_mask >> l) & 1u;
-            uint32_t cx, cy, cz;
-            float wx, wy, wz;
-            level_cell(x.x, N, cx, wx);
-            level_cell(x.y, N, cy, wy);
-            level_cell(x.z, N, cz, wz);
-            float2* gtab = gtables + (size_t)l * c.T;
-            const float g0 = df[2 * l], g1 = df[2 * l + 1];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t slot = vertex_slot(cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1),
-                                                  N, dense, Tmask);
-                const float wk = corner_weight(k, wx, wy, wz);
-                atomicAdd(gtab + slot, make_float2(wk * g0, wk * g1));
-            }
-        }
-    }
-}
-
-// Warp-cooperative form of hash_scatter, called by all 32 lanes (lanes with
-// valid = false contribute nothing).  Consecutive samples of a ray fall into the
+// dL/dtable[l][slot_k] += w_k * dL/df_l for every corner and level (FP32 vector
+// reductions of 8 bytes, one per corner), warp-cooperative: called by all 32 lanes
+// (lanes with valid = false contribute nothing).  Consecutive samples of a ray fall into the
 // same cell of the coarse levels, so per level the lanes with equal cells (runs of
 // consecutive lanes) first sum their 8 corner contributions with a segmented
 // shuffle reduction, and only the first lane of each run issues the 8 atomics.
