@@ -475,6 +475,9 @@ NCU_TRAFFIC = {
     "samples": 15869619,
     "field_fwd": 312187904 + 1244495360,
     "field_bwd": 1720803584 + 207130880,
+    # sm__pipe_tensor_cycles_active (share of peak, elapsed) of one launch on the
+    # 32768-ray case under `ncu --set full`
+    "tensor_pipe": {"field_fwd": 0.0349, "field_bwd": 0.0800},
 }
 
 
@@ -500,6 +503,14 @@ def measured_traffic(kernel, precision, n_samples):
     if kernel_sources_digest() != NCU_TRAFFIC["sha256"]:
         return None
     return NCU_TRAFFIC[kernel] * n_samples / NCU_TRAFFIC["samples"]
+
+
+def measured_tensor_pipe(precision):
+    """The tensor pipe's active share of the FP16 field kernels from the same ncu
+    captures, or None when the kernel sources changed since."""
+    if precision != "fp16" or kernel_sources_digest() != NCU_TRAFFIC["sha256"]:
+        return None
+    return dict(NCU_TRAFFIC["tensor_pipe"], source="ncu --set full, one launch of the 32768-ray case")
 
 
 def main():
@@ -584,6 +595,7 @@ def main():
     achieved = ab[dom] / (cand[dom] / 1e3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": measured_traffic(dom, args.precision, n_samples),
+            "tensor_pipe_active": measured_tensor_pipe(args.precision),
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "phase_ms_per_step": {k: v["ms"] / max(v["count"], 1) for k, v in prof.items() if v["count"]}}
     # the tables are L2-resident: also compare the table traffic with the measured
