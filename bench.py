@@ -471,13 +471,13 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 # kernel sources are the ones captured: the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
-    "sha256": "6057ea404e3069d1f0d3e85a391a96ab192d86dd448012cf137d05b006064259",
+    "sha256": "44ebc5f7f8c71669e2ef80105c1777f421e709cc3d24159a84614e40344a16e4",
     "samples": 15869619,
-    "field_fwd": 312187904 + 1244495360,
-    "field_bwd": 1720803584 + 207130880,
+    "field_fwd": 312295424 + 1244854272,
+    "field_bwd": 1720045056 + 207672320,
     # sm__pipe_tensor_cycles_active (share of peak, elapsed) of one launch on the
-    # 32768-ray case under `ncu --set full`
-    "tensor_pipe": {"field_fwd": 0.0349, "field_bwd": 0.0800},
+    # 32768-ray case (ncu --metrics sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed)
+    "tensor_pipe": {"field_fwd": 0.0349, "field_bwd": 0.0792},
 }
 
 
@@ -510,7 +510,7 @@ def measured_tensor_pipe(precision):
     captures, or None when the kernel sources changed since."""
     if precision != "fp16" or kernel_sources_digest() != NCU_TRAFFIC["sha256"]:
         return None
-    return dict(NCU_TRAFFIC["tensor_pipe"], source="ncu --set full, one launch of the 32768-ray case")
+    return dict(NCU_TRAFFIC["tensor_pipe"], source="ncu, one launch of the 32768-ray case")
 
 
 def main():
