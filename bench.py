@@ -471,13 +471,13 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 # kernel sources are the ones captured: the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
-    "sha256": "44ebc5f7f8c71669e2ef80105c1777f421e709cc3d24159a84614e40344a16e4",
+    "sha256": "ea610a94cbb14858b229bda7e5982da77fe79d973e595c2b6ba12362664e7adc",
     "samples": 15869619,
-    "field_fwd": 312295424 + 1244854272,
-    "field_bwd": 1720045056 + 207672320,
+    "field_fwd": 312883968 + 1244670208,
+    "field_bwd": 1720428288 + 208510720,
     # sm__pipe_tensor_cycles_active (share of peak, elapsed) of one launch on the
     # 32768-ray case (ncu --metrics sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed)
-    "tensor_pipe": {"field_fwd": 0.0349, "field_bwd": 0.0792},
+    "tensor_pipe": {"field_fwd": 0.0352, "field_bwd": 0.0812},
 }
 
 

@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
             }
             if (k + 1 < n_mine) publish();            // next tile's inputs; the MLP group starts on it
             if (k + 1 < n_mine) nb_arrive(kBarDfFree, 256);
-            hash_scatter_warp(c, gtables, x_done, v, valid_done);
+            hash_scatter_warp<true>(c, gtables, x_done, v, valid_done);
             if (kPose && valid_done) {
                 const float3 gx = hash_grad_x(c, reinterpret_cast<const float2*>(params), x_done, v);
                 pose_s[2 * (size_t)i_done] =
