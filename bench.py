@@ -467,7 +467,7 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # FP16 tensor-core field kernels on this workload (2^18 rays, 15,869,619 samples),
 # from one ncu capture of `python bench.py --steps 2 --warmup 1 --no-cpu-baseline
-# --no-forms --no-serving` with those two metrics (one pass).  Valid only while the
+# --no-forms --no-serving --no-large-map` with those two metrics (one pass).  Valid only while the
 # kernel sources are the ones captured: the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
