@@ -93,3 +93,30 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f
                 assert "oracle/" not in txt, f
+
+
+def _header_defines():
+    src = open(os.path.join(ROOT, "include", "nerfmap.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(MAP_\w+)\s+\(?(-?\d+)u?\)?", src)}
+
+
+def test_binding_constants_match_the_header():
+    """The binding's status codes, memory kinds, step flags, precisions, phases and
+    serving request kinds are the header's values (a drifted constant would pass
+    the wrong flag or misread a status without any other test noticing)."""
+    from paper_2210_13641_gb300 import binding
+    d = _header_defines()
+    for name in ("MAP_OK", "MAP_EINVAL", "MAP_ENOMEM", "MAP_ENOKF", "MAP_ETIMEOUT", "MAP_ECUDA",
+                 "MAP_MEM_HOST", "MAP_MEM_DEVICE", "MAP_STEP_NO_UPDATE", "MAP_STEP_POSE_GRAD"):
+        assert getattr(binding, name) == d[name], name
+    assert binding.PRECISION == {"fp32": d["MAP_PREC_FP32"], "fp16": d["MAP_PREC_FP16"], "bf16": d["MAP_PREC_BF16"]}
+    assert (binding.REQ_KEYFRAME, binding.REQ_STEP, binding.REQ_RENDER) == \
+        (d["MAP_REQ_KEYFRAME"], d["MAP_REQ_STEP"], d["MAP_REQ_RENDER"])
+    ph = {k: v for k, v in d.items() if k.startswith("MAP_PH_")}
+    assert len(binding.PHASES) == d["MAP_PHASES"] == len(ph)
+    order = ["MAP_PH_RAYGEN", "MAP_PH_MARCH", "MAP_PH_FIELD_FWD", "MAP_PH_COMPOSITE", "MAP_PH_FIELD_BWD",
+             "MAP_PH_ADAM", "MAP_PH_OCC", "MAP_PH_OUTPUT"]
+    assert [ph[k] for k in order] == list(range(len(order)))
+    assert binding.PHASES[ph["MAP_PH_FIELD_BWD"]] == "field_bwd" and binding.PHASES[ph["MAP_PH_ADAM"]] == "adam"
+    assert binding.MapConfig.level_res.size == 4 * d["MAP_MAX_LEVELS"]
