@@ -51,7 +51,11 @@ def parse():
     p.add_argument("--rays", type=int, default=N_RAYS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
+    # rays of one oracle step: the reference arm times K + W such steps (2048 rays, about
+    # 2 s each on the GPU machine's host cores); the cpu_baseline leg times one larger step
+    # (16384 rays, about 15 s there)
     p.add_argument("--sample-rays", type=int, default=2048, help=argparse.SUPPRESS)
+    p.add_argument("--cpu-sample-rays", type=int, default=16384, help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -527,7 +531,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(args.sample_rays)       # before any CUDA work in this process
+        cpu = run_cpu_baseline(args.cpu_sample_rays)   # before any CUDA work in this process
 
     import numpy as np
     import torch
