@@ -142,6 +142,25 @@ typedef struct map_stats {
 #define MAP_PHASES 8
 
 /*
+ * map_config_init - a configuration holding the library's defaults and the level
+ * table of the multiresolution grid (the Instant-NGP encoding that is the map of
+ * Sec. 3.4): N_l = floor(n_min * b^l) for l < n_levels, b = growth when growth > 0,
+ * else b = exp(ln(n_max / n_min) / (n_levels - 1)), evaluated in FP64 with a 1e-9
+ * relative nudge so that products which are whole numbers in exact arithmetic
+ * (e.g. 16 * 128) do not floor one below.  Also sets n_features = 2, log2_table,
+ * the MLP widths (32, 64, 16, 64), lambda_d = 1, Adam lr = 1e-2, beta = (0.9, 0.99),
+ * eps = 1e-15, occupancy decay 0.95 / threshold 0.01 / refresh every 16 steps,
+ * render_t_min = 1e-4, max_samples = 128, precision MAP_PREC_FP16, seed 0.  The
+ * scene fields (near_t, step_t, n_steps, grid_origin, grid_inv_size, box_max,
+ * occ_res) are left zero for the caller to set.  Host only: no device is used.
+ * Errors: MAP_EINVAL (message in map_last_error(NULL)) for a null cfg, n_levels
+ * outside 1..16, log2_table outside 10..24, n_min < 2, growth <= 0 with
+ * n_max <= n_min while n_levels > 1, or a level above 2^20.
+ */
+int map_config_init(map_config* cfg, uint32_t n_levels, uint32_t log2_table, uint32_t n_min, uint32_t n_max,
+                    double growth);
+
+/*
  * map_create - allocate a map on the current device.
  * cfg: configuration (validated: 1 <= n_levels <= 16 (n_levels * n_features <= 32),
  *   n_features == 2, 10 <= log2_table <= 24, level_res[l] >= 2, widths as above,
@@ -319,9 +338,11 @@ int map_profile_read(map_handle h, double* ms, uint64_t* count, uint64_t* launch
  * scan totals) is a static device array of about 4 MB that every GPU loading the
  * library holds until the process exits.
  *
- * cfg: the march fields are used (near_t, step_t, n_steps, max_samples,
- *   grid_origin, grid_inv_size, box_max, occ_res).  occ_bits: device bitfield
- *   (layout as map_set_occupancy), required when occ_res > 0, ignored otherwise.
+ * cfg: the march fields are used (near_t, step_t, n_steps <= 65536, max_samples
+ *   <= 1024, grid_origin, grid_inv_size, box_max, occ_res).  occ_bits: device
+ *   bitfield (layout as map_set_occupancy), read as 32-bit words, so it must be
+ *   4-byte aligned; required when occ_res > 0, ignored otherwise.  Every device
+ *   array of this call must be 4-byte aligned (misaligned: MAP_EINVAL, no launch).
  * rays_o, rays_d: device arrays [n_rays][3] (origin, unit direction).
  * n_rays: 1 .. 1048576 (the scratch size); larger values fail with MAP_EINVAL.
  * offsets: device [n_rays + 1], receives the exclusive scan of the per-ray sample
@@ -333,7 +354,7 @@ int map_profile_read(map_handle h, double* ms, uint64_t* count, uint64_t* launch
  * capture.  All calls share the scratch array: calls that overlap on the GPU
  * (other streams, other host threads) race and must be serialised by the caller.
  * Errors: MAP_EINVAL (argument), MAP_ECUDA (address lookup or launch); the message
- * is available from map_last_error(NULL) until this thread's next successful call.
+ * is available from map_last_error(NULL) (see there).
  */
 int map_march_noalloc(const map_config* cfg, const uint8_t* occ_bits, const float* rays_o,
                       const float* rays_d, uint32_t n_rays, uint32_t* offsets, uint32_t* ray_id,
@@ -431,7 +452,9 @@ int map_server_get_stats(map_server s, map_server_stats* out);
  * own copy of the struct has the same layout. */
 size_t map_abi_config_size(void);
 
-/* Message of the last failure on h (h = NULL: of the last failed map_create). */
+/* Message of the last failure on h.  h = NULL: the message of this host thread's
+ * most recent call that takes no map handle (map_create, map_march_noalloc,
+ * map_marginal_covariances), or "" when that call succeeded. */
 const char* map_last_error(map_handle h);
 
 #ifdef __cplusplus

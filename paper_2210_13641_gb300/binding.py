@@ -9,7 +9,6 @@ fallback.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 from typing import Optional
 
@@ -81,6 +80,8 @@ PHASES = ["ray_gen", "march", "field_fwd", "composite", "field_bwd", "adam", "oc
 
 
 _SIGS = {
+    "map_config_init": (ctypes.c_int, [ctypes.POINTER(MapConfig), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.c_double]),
     "map_create": (ctypes.c_int, [ctypes.POINTER(MapConfig), ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
     "map_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "map_add_keyframe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
@@ -199,25 +200,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 
 # ------------------------------------------------------------------ config helpers
 
-def level_resolutions(n_levels: int, n_min: int, growth: Optional[float] = None,
-                      n_max: Optional[int] = None) -> list:
-    """N_l = floor(N_min * b^l) with b = growth or (N_max/N_min)^(1/(L-1)); a 1e-9
-    relative nudge keeps exact integers (e.g. 16 * 128 = 2048) from flooring below."""
-    if growth is None:
-        growth = (n_max / n_min) ** (1.0 / (n_levels - 1)) if n_levels > 1 else 1.0
-    return [int(math.floor(n_min * growth ** l * (1.0 + 1e-9))) for l in range(n_levels)]
-
-
 def make_config(cfg, occ_every: Optional[int] = None) -> MapConfig:
-    """C configuration from a field-config object (attributes as in the header)."""
+    """C configuration from a field-config object (attributes as in the header);
+    the level table comes from the library (map_config_init)."""
+    lib = load()
     c = MapConfig()
-    c.n_levels = cfg.n_levels
-    c.n_features = cfg.n_features
-    c.log2_table = cfg.log2_table
-    res = level_resolutions(cfg.n_levels, cfg.n_min, cfg.growth, cfg.n_max)
-    for l, n in enumerate(res):
-        c.level_res[l] = n
-    c.enc_width, c.density_hidden, c.geo_width, c.color_hidden = 32, 64, 16, 64
+    rc = lib.map_config_init(ctypes.byref(c), cfg.n_levels, cfg.log2_table, cfg.n_min, cfg.n_max or 0,
+                             float(cfg.growth) if cfg.growth is not None else 0.0)
+    if rc != MAP_OK:
+        raise MapError(rc, lib.map_last_error(None).decode())
+    if (cfg.n_features, cfg.enc_width, cfg.density_hidden, cfg.geo_width, cfg.color_hidden) != (2, 32, 64, 16, 64):
+        raise ValueError("the library's field has F = 2 and MLP widths 32/64/16/64")
     c.near_t = float(cfg.near)
     c.step_t = float(cfg.step)
     c.n_steps = cfg.n_steps
@@ -236,6 +229,12 @@ def make_config(cfg, occ_every: Optional[int] = None) -> MapConfig:
     c.precision = PRECISION[cfg.precision]
     c.seed = cfg.seed
     return c
+
+
+def level_resolutions(cfg) -> list:
+    """The level table the library computes for a field config (map_config_init)."""
+    c = make_config(cfg)
+    return [int(c.level_res[l]) for l in range(cfg.n_levels)]
 
 
 def pack_params(named: dict) -> np.ndarray:

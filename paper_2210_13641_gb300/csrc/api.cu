@@ -12,12 +12,9 @@
 
 using namespace nm;
 
-const char* nm_noalloc_last_error();
-const char* nm_cov_last_error();
-
 namespace {
 
-thread_local std::string g_create_error;
+thread_local std::string g_global_error;
 
 struct Keyframe {
     uint32_t id, W, H;
@@ -83,7 +80,7 @@ namespace {
 
 int fail(map_scene* h, int code, const std::string& msg) {
     if (h) h->err = msg;
-    else g_create_error = msg;
+    else g_global_error = msg;
     return code;
 }
 
@@ -150,7 +147,7 @@ int ensure_step_bufs(map_scene* h, uint32_t n_rays) {
     StepBufs b{};
     const uint32_t cap = std::max<uint32_t>(n_rays, 1024);
     const uint64_t cs = (uint64_t)cap * h->cfg.max_samples;
-    const uint32_t n_tiles = (cap + 4095) / 4096;
+    const uint32_t n_tiles = (cap + kScanTile - 1) / kScanTile;
     struct Req { void** p; size_t bytes; };
     std::vector<Req> reqs = {
         {(void**)&b.rays, sizeof(float) * kRayPlanes * cap},
@@ -278,10 +275,56 @@ void prof_clear(map_scene* h) {
 
 }  // namespace
 
+namespace nm {
+void clear_global_error() { g_global_error.clear(); }
+void set_global_error(const char* msg) { g_global_error = msg; }
+}  // namespace nm
+
 extern "C" {
+
+int map_config_init(map_config* cfg, uint32_t n_levels, uint32_t log2_table, uint32_t n_min, uint32_t n_max,
+                    double growth) {
+    g_global_error.clear();
+    if (!cfg) return fail(nullptr, MAP_EINVAL, "map_config_init: null config");
+    if (n_levels < 1 || n_levels > 16) return fail(nullptr, MAP_EINVAL, "map_config_init: n_levels must be 1..16");
+    if (log2_table < 10 || log2_table > 24) return fail(nullptr, MAP_EINVAL, "map_config_init: log2_table must be 10..24");
+    if (n_min < 2) return fail(nullptr, MAP_EINVAL, "map_config_init: n_min must be >= 2");
+    double b = 1.0;
+    if (growth > 0.0) b = growth;
+    else if (n_levels > 1) {
+        if (n_max <= n_min) return fail(nullptr, MAP_EINVAL, "map_config_init: need growth > 0 or n_max > n_min");
+        b = std::exp(std::log((double)n_max / (double)n_min) / (double)(n_levels - 1));
+    }
+    std::memset(cfg, 0, sizeof(*cfg));
+    for (uint32_t l = 0; l < n_levels; ++l) {
+        const double N = std::floor((double)n_min * std::pow(b, (double)l) * (1.0 + 1e-9));
+        if (N > (double)(1u << 20)) return fail(nullptr, MAP_EINVAL, "map_config_init: a level exceeds 2^20");
+        cfg->level_res[l] = (uint32_t)N;
+    }
+    cfg->n_levels = n_levels;
+    cfg->n_features = 2;
+    cfg->log2_table = log2_table;
+    cfg->enc_width = kEnc;
+    cfg->density_hidden = kHid;
+    cfg->geo_width = kGeo;
+    cfg->color_hidden = kHid;
+    cfg->max_samples = 128;
+    cfg->occ_every = 16;
+    cfg->occ_decay = 0.95f;
+    cfg->occ_thresh = 0.01f;
+    cfg->lambda_d = 1.f;
+    cfg->lr = 1e-2f;
+    cfg->beta1 = 0.9f;
+    cfg->beta2 = 0.99f;
+    cfg->eps = 1e-15f;
+    cfg->render_t_min = 1e-4f;
+    cfg->precision = MAP_PREC_FP16;
+    return MAP_OK;
+}
 
 int map_create(const map_config* cfg, size_t hbm_budget_bytes, map_handle* out) {
     std::string why;
+    g_global_error.clear();
     if (!out) return fail(nullptr, MAP_EINVAL, "null output handle");
     *out = nullptr;
     if (validate(cfg, why) != MAP_OK) return fail(nullptr, MAP_EINVAL, why);
@@ -305,7 +348,7 @@ int map_create(const map_config* cfg, size_t hbm_budget_bytes, map_handle* out) 
         if (!rc) rc = dalloc(h, (void**)&h->occ_density, h->n_cells * sizeof(float));
     }
     if (rc) {
-        g_create_error = h->err;
+        g_global_error = h->err;
         map_destroy(h);
         return rc;
     }
@@ -319,7 +362,7 @@ int map_create(const map_config* cfg, size_t hbm_budget_bytes, map_handle* out) 
     launch_init_params(h->params, h->n_table, cfg->seed, nullptr);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        g_create_error = std::string("init: ") + cudaGetErrorString(e);
+        g_global_error = std::string("init: ") + cudaGetErrorString(e);
         map_destroy(h);
         return MAP_ECUDA;
     }
@@ -871,11 +914,7 @@ int map_profile_read(map_handle h, double* ms, uint64_t* count, uint64_t* launch
 size_t map_abi_config_size(void) { return sizeof(map_config); }
 
 const char* map_last_error(map_handle h) {
-    if (h) return h->err.c_str();
-    const char* m = nm_noalloc_last_error();
-    if (m[0]) return m;
-    const char* cv = nm_cov_last_error();
-    return cv[0] ? cv : g_create_error.c_str();
+    return h ? h->err.c_str() : g_global_error.c_str();
 }
 
 }  // extern "C"

@@ -9,6 +9,12 @@
 
 namespace nm {
 
+// Message slot of the calls that take no map handle (map_create,
+// map_march_noalloc, map_marginal_covariances), read by map_last_error(NULL): one
+// slot per host thread, cleared when such a call starts and set when it fails.
+void clear_global_error();
+void set_global_error(const char* msg);
+
 // One keyframe in the device store.  texels: 8 floats per pixel
 // {r, g, b, D, Sigma_D, 0, 0, 0} (one 32-byte sector), D and Sigma_D in ray units.
 struct KfDesc {
@@ -23,6 +29,12 @@ struct KfDesc {
 enum RayPlane { kOx = 0, kOy, kOz, kDx, kDy, kDz, kIr, kIg, kIb, kD, kV, kKf, kRayPlanes };
 
 constexpr uint32_t kCompositeMaxBlocks = 4096;
+
+// Exclusive scan of per-ray counts (k_rays.cu): one 1024-thread block scans a tile of
+// kScanTile counts and writes the tile's total; a second pass scans the totals.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
 
 struct StepBufs {
     float* rays;            // [kRayPlanes][cap_rays]
@@ -55,6 +67,7 @@ void launch_ray_gen_view(const float* c2w, const float* K, uint32_t W, uint32_t 
 void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, const StepBufs& b,
                   cudaStream_t s);
 
+// tile_sums: at least ceil(n / kScanTile) words.
 void launch_scan_counts(const uint32_t* counts, uint32_t n, uint32_t* offsets, uint32_t* tile_sums,
                         cudaStream_t s);
 

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "nerfmap.h"
+#include "internal.h"
 
 namespace nm {
 
@@ -30,13 +31,7 @@ constexpr uint32_t kCovMaxC = 144;  // 24 keyframes
 constexpr uint32_t kCovMaxB = 8;
 constexpr int kCovThreads = 1024;
 
-thread_local char g_cov_error[160] = {0};
-
-void set_cov_error(const char* msg) {
-    size_t i = 0;
-    for (; msg[i] && i + 1 < sizeof(g_cov_error); ++i) g_cov_error[i] = msg[i];
-    g_cov_error[i] = 0;
-}
+void set_cov_error(const char* msg) { set_global_error(msg); }
 
 __device__ __forceinline__ uint32_t tri(uint32_t i, uint32_t j) { return i * (i + 1) / 2 + j; }  // i >= j
 
@@ -175,13 +170,10 @@ struct DevBuf {
 
 using namespace nm;
 
-// Message of this thread's last failed map_marginal_covariances call ("" after a
-// success); used by map_last_error(NULL).
-const char* nm_cov_last_error() { return g_cov_error; }
-
 extern "C" int map_marginal_covariances(const double* C, uint32_t c, const double* P, uint32_t p,
                                         const int32_t* blk, const double* e, uint32_t B, double* sigma_T,
                                         double* sigma_d, int mem_kind, void* stream) {
+    clear_global_error();
     if (!C || !P || !blk || !e || !sigma_T || !sigma_d) {
         set_cov_error("map_marginal_covariances: null argument");
         return MAP_EINVAL;
@@ -269,6 +261,5 @@ extern "C" int map_marginal_covariances(const double* C, uint32_t c, const doubl
         set_cov_error("map_marginal_covariances: the reduced camera matrix is not positive definite");
         return MAP_EINVAL;
     }
-    g_cov_error[0] = 0;
     return MAP_OK;
 }

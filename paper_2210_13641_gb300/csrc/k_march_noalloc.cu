@@ -24,8 +24,11 @@
 namespace nm {
 
 constexpr uint32_t kMarchNoAllocMaxRays = 1u << 20;
-constexpr uint32_t kMarchNoAllocTiles = (kMarchNoAllocMaxRays + 4095) / 4096;  // scan tiles of 4096
+// one tile total per scan tile of the largest call
+constexpr uint32_t kMarchNoAllocTiles = (kMarchNoAllocMaxRays + kScanTile - 1) / kScanTile;
 constexpr uint32_t kMarchScratchWords = kMarchNoAllocMaxRays + kMarchNoAllocTiles;
+static_assert((uint64_t)kMarchNoAllocTiles * kScanTile >= kMarchNoAllocMaxRays,
+              "the tile-total scratch must cover every scan tile of the largest call");
 
 // counts[0 .. 2^20) then the scan's tile totals.  Every word a call reads is first
 // written by the same call (counts by the count pass, tile totals by the scan), so
@@ -37,13 +40,9 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 uint32_t* g_scratch_addr[kMaxDevices] = {};
-thread_local char g_noalloc_error[160] = {0};
+void set_error(const char* msg) { set_global_error(msg); }
 
-void set_error(const char* msg) {
-    size_t i = 0;
-    for (; msg[i] && i + 1 < sizeof(g_noalloc_error); ++i) g_noalloc_error[i] = msg[i];
-    g_noalloc_error[i] = 0;
-}
+bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
 
 // Device address of the scratch array on the current device (looked up once per
 // device, with that device current).
@@ -68,6 +67,8 @@ cudaError_t scratch_address(uint32_t** out) {
 // Same march as the mapping step (step i of a ray at t_i = near + i * step, kept
 // inside the box and in occupied cells, first max_samples kept), reading the rays
 // as [n][3] arrays.  Pass 1 counts, pass 2 writes (ray, t) at the scanned offsets.
+// Only the steps of the ray's conservative box step range are tested (the range
+// contains every step whose position passes the box test), as in the map's march.
 template <bool kEmit>
 __global__ void k_march_rows(DevCfg c, const uint32_t* __restrict__ bits, uint32_t n_rays,
                              const float* __restrict__ ro, const float* __restrict__ rd,
@@ -77,9 +78,11 @@ __global__ void k_march_rows(DevCfg c, const uint32_t* __restrict__ bits, uint32
     if (r >= n_rays) return;
     const float3 o = make_float3(ro[3 * r], ro[3 * r + 1], ro[3 * r + 2]);
     const float3 d = make_float3(rd[3 * r], rd[3 * r + 1], rd[3 * r + 2]);
+    uint32_t i_lo, i_hi;
+    box_step_range(c, o, d, i_lo, i_hi);
     uint32_t n = 0;
     const uint32_t base = kEmit ? offsets[r] : 0;
-    for (uint32_t i = 0; i < c.n_steps && n < c.max_samples; ++i) {
+    for (uint32_t i = i_lo; i < i_hi && n < c.max_samples; ++i) {
         const float t = sample_t(c, i);
         const float3 x = grid_pos(c, o, d, t);
         if (!in_box(c, x) || !occupied(c, bits, x)) continue;
@@ -99,15 +102,24 @@ using namespace nm;
 extern "C" int map_march_noalloc(const map_config* cfg, const uint8_t* occ_bits, const float* rays_o,
                                  const float* rays_d, uint32_t n_rays, uint32_t* offsets, uint32_t* ray_id,
                                  float* t, size_t cap_samples, void* stream) {
+    clear_global_error();
     if (!cfg || !rays_o || !rays_d || !offsets || !ray_id || !t) {
         set_error("map_march_noalloc: null pointer argument");
+        return MAP_EINVAL;
+    }
+    // the kernels read the bitfield as 32-bit words and the other arrays as 4-byte
+    // values: a misaligned address would fault on the device, so it is refused here
+    if (!aligned4(rays_o) || !aligned4(rays_d) || !aligned4(offsets) || !aligned4(ray_id) || !aligned4(t) ||
+        (cfg->occ_res && occ_bits && !aligned4(occ_bits))) {
+        set_error("map_march_noalloc: every device array (occ_bits included) must be 4-byte aligned");
         return MAP_EINVAL;
     }
     if (n_rays == 0 || n_rays > kMarchNoAllocMaxRays) {
         set_error("map_march_noalloc: n_rays must be 1 .. 1048576 (the size of the static scratch)");
         return MAP_EINVAL;
     }
-    if (!(cfg->step_t > 0.f) || cfg->n_steps == 0 || cfg->max_samples == 0 || cfg->max_samples > 1024 ||
+    if (!(cfg->step_t > 0.f) || cfg->n_steps == 0 || cfg->n_steps > 65536 || cfg->max_samples == 0 ||
+        cfg->max_samples > 1024 ||
         !(cfg->grid_inv_size > 0.f) || cfg->occ_res % 8 != 0 || cfg->occ_res > 1024) {
         set_error("map_march_noalloc: invalid march fields in the configuration");
         return MAP_EINVAL;
@@ -150,10 +162,5 @@ extern "C" int map_march_noalloc(const map_config* cfg, const uint8_t* occ_bits,
         set_error("map_march_noalloc: kernel launch failed");
         return MAP_ECUDA;
     }
-    g_noalloc_error[0] = 0;
     return MAP_OK;
 }
-
-// Message of this thread's last failed map_march_noalloc call ("" if its last
-// call succeeded); used by map_last_error(NULL).
-const char* nm_noalloc_last_error() { return g_noalloc_error; }

@@ -176,9 +176,6 @@ __global__ void k_compact(uint32_t n_rays, uint32_t max_samples, const uint32_t*
 
 // Exclusive scan of counts[0..n) into offsets[0..n], offsets[n] = total.
 // Level 1: each 1024-thread block scans 4096 entries and writes its block total.
-constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 4;
-constexpr int kScanTile = kScanThreads * kScanPer;
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
                                                          uint32_t& total) {

@@ -57,9 +57,9 @@ def test_create_without_gpu_fails_cleanly(lib):
 def test_invalid_configs_rejected_before_device_use(lib):
     from paper_2210_13641_gb300 import binding
     for bad in (dict(n_levels=0), dict(log2_table=30), dict(max_samples=0), dict(occ_res=12)):
-        c = binding.make_config(synth.config_small().replace(**{k: v for k, v in bad.items() if k != "n_levels"}))
-        if "n_levels" in bad:
-            c.n_levels = 0
+        c = binding.make_config(synth.config_small())
+        for k, v in bad.items():
+            setattr(c, k, v)
         h = ctypes.c_void_p()
         rc = lib.map_create(ctypes.byref(c), 0, ctypes.byref(h))
         assert rc == binding.MAP_EINVAL, bad
@@ -67,11 +67,36 @@ def test_invalid_configs_rejected_before_device_use(lib):
 
 
 @pytest.mark.parametrize("mk", [synth.config_small, synth.config_c1, synth.config_c2, synth.config_c5])
-def test_level_table_matches_oracle(mk):
+def test_level_table_matches_oracle(lib, mk):
+    """The library's level table (map_config_init, host only) equals the oracle's."""
     from paper_2210_13641_gb300 import binding
     cfg = mk()
-    assert binding.level_resolutions(cfg.n_levels, cfg.n_min, cfg.growth, cfg.n_max) == \
-        oracle.level_resolutions(cfg)
+    assert binding.level_resolutions(cfg) == oracle.level_resolutions(cfg)
+
+
+def test_config_init_defaults_and_refusals(lib):
+    from paper_2210_13641_gb300 import binding
+    c = binding.MapConfig()
+    assert lib.map_config_init(ctypes.byref(c), 16, 19, 16, 2048, 0.0) == 0
+    assert lib.map_last_error(None) == b""
+    assert (c.n_features, c.enc_width, c.density_hidden, c.geo_width, c.color_hidden) == (2, 32, 64, 16, 64)
+    assert c.level_res[0] == 16 and c.level_res[15] == 2048 and c.level_res[16] == 0
+    assert c.precision == binding.PRECISION["fp16"] and c.max_samples == 128 and c.step_t == 0.0
+    for args in ((0, 19, 16, 2048, 0.0), (17, 19, 16, 2048, 0.0), (16, 9, 16, 2048, 0.0), (16, 19, 1, 2048, 0.0),
+                 (16, 19, 16, 16, 0.0), (16, 19, 16, 0, -1.0), (16, 19, 2, 0, 4.0)):
+        assert lib.map_config_init(ctypes.byref(c), *args) == binding.MAP_EINVAL, args
+        assert lib.map_last_error(None).startswith(b"map_config_init"), args
+    assert lib.map_config_init(None, 16, 19, 16, 2048, 0.0) == binding.MAP_EINVAL
+
+
+def test_march_noalloc_allocates_nothing_in_source():
+    """The allocation-free march's translation unit calls no allocating routine
+    (comments aside): no cudaMalloc / cudaFree in any form, no cudaMallocHost."""
+    src = open(os.path.join(ROOT, "paper_2210_13641_gb300", "csrc", "k_march_noalloc.cu")).read()
+    code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", src, flags=re.S))
+    assert "cudaGetSymbolAddress" in code
+    for bad in ("cudaMalloc", "cudaFree", "cuMemAlloc", "cuMemFree", "malloc(", "new "):
+        assert bad not in code, bad
 
 
 def test_pack_unpack_roundtrip():
