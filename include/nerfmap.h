@@ -69,8 +69,9 @@ extern "C" {
  * whose (N_l + 1)^3 vertices fit in its table is indexed densely, otherwise by the
  * spatial hash (x * 1 ^ y * 2654435761 ^ z * 805459861) mod 2^log2_table.
  * MLP widths are fixed: enc_width 32 (L * F zero padded), density_hidden 64,
- * geo_width 16, color_hidden 64.  Density sigma = exp(min(h_0, 15)) (the truncated
- * exponential of Instant-NGP), colour = sigmoid of the colour MLP's output.
+ * geo_width 16, color_hidden 64.  Density sigma = exp(min(h_0, 15)) (an exponential
+ * with its value capped: beyond h_0 = 15 a sample is opaque already; dsigma/dh_0 = 0
+ * above the cap), colour = sigmoid of the colour MLP's output.
  *
  * Sampling (Sec. 3.2, sampling 3D positions along the pixel's ray): step i of a
  * ray is at t_i = near_t + i * step_t, i < n_steps, grid position
@@ -447,6 +448,19 @@ int map_server_submit_render(map_server s, uint32_t scene, const float c2w[12], 
 /* Up to cap finished requests, oldest first. */
 int map_server_poll(map_server s, map_completion* out, uint32_t cap, uint32_t* n_out);
 int map_server_get_stats(map_server s, map_server_stats* out);
+
+/*
+ * map_set_wait_polls - the poll limit of every bounded wait of this map's
+ * tensor-core kernels for the completion of their MMAs (default 2^24 polls).  No
+ * counterpart in the paper: it exists to test the timeout path.  When a wait runs
+ * out, the kernel stops waiting, skips the rest of its work (results of that step
+ * or render are garbage: gradients, renders and the loss), waits for the MMAs it
+ * has issued, frees its tensor memory and sets a device flag; the next call that
+ * waits for the stream (map_step with out_loss, map_render with host outputs)
+ * returns MAP_ETIMEOUT and clears the flag, and the map stays usable.  polls = 0
+ * makes every wait expire at once.  Takes effect for the following calls.
+ */
+int map_set_wait_polls(map_handle h, uint32_t polls);
 
 /* sizeof(map_config) as compiled into the library, so a binding can check that its
  * own copy of the struct has the same layout. */

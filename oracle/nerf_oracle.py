@@ -281,73 +281,74 @@ def sh_deg4(d: np.ndarray) -> np.ndarray:
 
 # ------------------------------------------------------------------ a5, a6: MLPs
 
-# Density activation: the truncated exponential of Instant-NGP (the map the paper
-# uses), sigma = exp(min(h_0, 15)).  Beyond h_0 = 15 a sample is opaque already
-# (sigma * delta > 10^4 at any spacing used here); the cap keeps sigma finite in FP32
-# and its derivative there is zero.
+# Density activation: sigma = exp(min(h_0, 15)), the exponential with its value
+# capped (a reading: the paper defers the activation to its map).  Beyond h_0 = 15 a
+# sample is opaque already (sigma * delta > 10^4 at any spacing used here); the cap
+# keeps sigma finite in FP32 and its derivative there is zero.  (Instant-NGP's
+# "truncated exponential" is a different rule: it clamps only the argument of the
+# derivative.)
 SIGMA_H_MAX = 15.0
 
 def relu(a):
     return np.maximum(a, 0.0)
 
 
-def round_to(x, precision):
-    """Round to the MLP operand type: IEEE binary16 (saturating at +-65504) or
-    bfloat16 (round to nearest even of the float32 value); None: unchanged."""
-    x = np.asarray(x, np.float64)
+# MLP operand precision (the benchmark spec's precision pattern: the MLP multiplies
+# FP16 or BF16 operands and accumulates in FP32; everything else stays FP32).  The
+# oracle's model of such an MLP rounds every operand of every product - weights,
+# layer inputs and, in the backward pass, the gradient operands - to the operand
+# type's significand (11 bits for FP16, 8 for BF16, round to nearest even, exponent
+# range unbounded) and sums the products exactly (FP64).  It is a model of the
+# number format, not of any kernel: no scaling, no saturation, no accumulation
+# order.  With the rounding an identity it is the plain FP64 chain.
+MLP_BITS = {"fp16": 11, "bf16": 8}
+
+
+def bits_of(precision):
+    """Significand bits of an MLP precision name (None / "fp32": no rounding)."""
     if precision is None or precision == "fp32":
-        return x
-    if precision == "fp16":
-        return np.clip(x, -65504.0, 65504.0).astype(np.float16).astype(np.float64)
-    if precision == "bf16":
-        b = x.astype(np.float32).view(np.uint32).astype(np.uint64)
-        b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
-        return b.astype(np.uint32).view(np.float32).astype(np.float64)
-    raise ValueError(precision)
+        return None
+    if isinstance(precision, (int, np.integer)):
+        return int(precision)
+    return MLP_BITS[precision]
 
 
-FP16_FEATURE_SCALE = 256.0   # FP16 encodings enter the MLP as fp16(2^8 f)
+def round_sig(x, bits):
+    """x rounded to `bits` significant bits (round to nearest, ties to even), with
+    no exponent limit: x = m 2^e with 1/2 <= |m| < 1, m rounded to a multiple of
+    2^-bits.  Exact in FP64 for bits <= 53 (the rescalings are powers of two)."""
+    x = np.asarray(x, np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(np.ldexp(m, bits)), e - bits)
 
 
-def relu_decisions(P: dict, feat: np.ndarray, sh: np.ndarray, precision: str):
-    """The ReLU branch of every hidden unit as the FP16/BF16 MLP takes it: the same
-    layer chain on operands rounded to the MLP type (products summed exactly).  A
-    ReLU branch is an integer decided by floating point, so parity takes it in the
-    kernel's precision; the values themselves stay FP64 (field_forward)."""
-    R = lambda a: round_to(a, precision)
-    W = {k: R(P[k]) for k in ("W1", "W2", "W3", "W4", "W5")}
-    fs = FP16_FEATURE_SCALE if precision == "fp16" else 1.0
-    a1 = R(feat * fs) @ W["W1"].T / fs
-    h = R(relu(a1)) @ W["W2"].T
-    a3 = R(np.concatenate([h, sh], axis=1)) @ W["W3"].T
-    a4 = R(relu(a3)) @ W["W4"].T
-    return a1 > 0, a3 > 0, a4 > 0
-
-
-def field_forward(P: dict, feat: np.ndarray, sh: np.ndarray, decisions=None) -> dict:
+def field_forward(P: dict, feat: np.ndarray, sh: np.ndarray, bits=None) -> dict:
     """sigma_i and c_i from one evaluation of the MLPs at the sample (Sec. 3.2: both
     are estimated simultaneously).  Density MLP: h = W2 relu(W1 feat), sigma =
     exp(min(h_0, 15)).  Colour MLP on [h; SH]: c = sigmoid(W5 relu(W4 relu(W3 [h; SH]))).
-    No biases.  `decisions` (from relu_decisions) fixes the ReLU branches; by
-    default each unit is active when its FP64 pre-activation is positive.
-    Returns every intermediate (for the backward pass)."""
-    W = {k: P[k].astype(np.float64) for k in ("W1", "W2", "W3", "W4", "W5")}
-    a1 = feat @ W["W1"].T
-    m1 = a1 > 0 if decisions is None else decisions[0]
-    h1 = np.where(m1, a1, 0.0)
+    No biases.  With `bits` every MLP operand (weights and layer inputs) is rounded
+    to that many significant bits before its products (round_sig); sigma and the
+    colour come from the exactly summed products.  Returns every intermediate (the
+    rounded operands where rounded) for the backward pass."""
+    R = (lambda a: a) if bits is None else (lambda a: round_sig(a, bits))
+    W = {k: R(P[k].astype(np.float64)) for k in ("W1", "W2", "W3", "W4", "W5")}
+    f = R(np.asarray(feat, np.float64))
+    a1 = f @ W["W1"].T
+    m1 = a1 > 0
+    h1 = R(np.where(m1, a1, 0.0))
     h = h1 @ W["W2"].T
     sigma = np.exp(np.minimum(h[:, 0], SIGMA_H_MAX))
-    x3 = np.concatenate([h, sh], axis=1)
+    x3 = R(np.concatenate([h, sh], axis=1))
     a3 = x3 @ W["W3"].T
-    m3 = a3 > 0 if decisions is None else decisions[1]
-    h3 = np.where(m3, a3, 0.0)
+    m3 = a3 > 0
+    h3 = R(np.where(m3, a3, 0.0))
     a4 = h3 @ W["W4"].T
-    m4 = a4 > 0 if decisions is None else decisions[2]
-    h4 = np.where(m4, a4, 0.0)
+    m4 = a4 > 0
+    h4 = R(np.where(m4, a4, 0.0))
     z = h4 @ W["W5"].T
     rgb = 1.0 / (1.0 + np.exp(-z))
-    return dict(feat=feat, a1=a1, m1=m1, h1=h1, h=h, sigma=sigma, x3=x3, a3=a3, m3=m3, h3=h3,
-                a4=a4, m4=m4, h4=h4, z=z, rgb=rgb)
+    return dict(feat=f, a1=a1, m1=m1, h1=h1, h=h, sigma=sigma, x3=x3, a3=a3, m3=m3, h3=h3,
+                a4=a4, m4=m4, h4=h4, z=z, rgb=rgb, W=W, bits=bits)
 
 
 # ------------------------------------------------------------------ a7: compositing
@@ -431,14 +432,22 @@ def composite_backward_ray_abs(sigma, rgb, t, delta, w, Tcum, gI, gD):
 
 def field_backward(P: dict, fw: dict, dsigma, drgb, magnitude: bool = False, with_dsh: bool = False):
     """Chain rule through the MLPs (a10).  Returns weight gradients and dL/dfeat.
+    With a rounded forward (field_forward with bits) the gradient operands are
+    rounded the same way before their products: dL/dz, the masked dL/da of each
+    hidden layer and dL/dh (the density branch's input gradient, after the
+    dL/dsigma term is added).
     magnitude=True (with the absolute-term inputs of composite_backward_ray_abs)
     runs the same chain on |W| and on activation magnitudes (each activation
     replaced by the sum of the absolute values of its own terms, same ReLU
     branches): every output is then the sum of the absolute values of the products
     that make up the matching gradient entry, expanded down to the inputs - the
     scale of its rounding error in any summation order."""
-    W = {k: P[k].astype(np.float64) for k in ("W1", "W2", "W3", "W4", "W5")}
+    bits = fw.get("bits")
+    R = (lambda a: a) if bits is None else (lambda a: round_sig(a, bits))
+    W = fw["W"]
     if magnitude:
+        if bits is not None:
+            raise ValueError("magnitudes are defined for the plain chain only")
         W = {k: np.abs(v) for k, v in W.items()}
         f = np.abs(fw["feat"])
         h1 = np.where(fw["m1"], f @ W["W1"].T, 0.0)
@@ -447,20 +456,21 @@ def field_backward(P: dict, fw: dict, dsigma, drgb, magnitude: bool = False, wit
         h4 = np.where(fw["m4"], h3 @ W["W4"].T, 0.0)
         fw = dict(fw, feat=f, h1=h1, x3=x3, h3=h3, h4=h4)
     rgb = fw["rgb"]
-    dz = drgb * rgb * (1.0 - rgb)
+    dz = R(drgb * rgb * (1.0 - rgb))
     g = {"W5": dz.T @ fw["h4"]}
     dh4 = dz @ W["W5"]
-    da4 = dh4 * fw["m4"]
+    da4 = R(dh4 * fw["m4"])
     g["W4"] = da4.T @ fw["h3"]
     dh3 = da4 @ W["W4"]
-    da3 = dh3 * fw["m3"]
+    da3 = R(dh3 * fw["m3"])
     g["W3"] = da3.T @ fw["x3"]
     dx3 = da3 @ W["W3"]
     dh = dx3[:, :P["W2"].shape[0]].copy()
     dh[:, 0] += dsigma * fw["sigma"] * (fw["h"][:, 0] < SIGMA_H_MAX)
+    dh = R(dh)
     g["W2"] = dh.T @ fw["h1"]
     dh1 = dh @ W["W2"]
-    da1 = dh1 * fw["m1"]
+    da1 = R(dh1 * fw["m1"])
     g["W1"] = da1.T @ fw["feat"]
     dfeat = da1 @ W["W1"]
     if with_dsh:
@@ -483,12 +493,13 @@ def hash_backward(cfg, idx, wts, dfeat):
 
 def forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits=None,
                      level_res=None, rays=None, want_grad=True, magnitudes=False,
-                     decide_in=None):
+                     mlp_bits=None):
     """a1-a11: loss L_M and its gradient for one batch.  Returns a dict with the
     loss, per-ray renders, the sample list and the named gradients; with
     magnitudes=True also `grads_abs`, per entry the sum of the absolute values of
-    the products that form it (see field_backward).  decide_in = "fp16" | "bf16"
-    takes the ReLU branches in that MLP precision (relu_decisions)."""
+    the products that form it (see field_backward).  mlp_bits = "fp16" | "bf16" (or
+    a bit count) evaluates the MLPs with operands rounded to that precision
+    (field_forward / field_backward); None is the plain FP64 chain."""
     level_res = level_resolutions(cfg) if level_res is None else level_res
     if rays is None:
         kf, u, v = draw_rays(seed, step, n_rays, [(k.W, k.H) for k in keyframes])
@@ -501,8 +512,7 @@ def forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits=None,
     ray_id, step_idx, t, x = march(cfg, o, d, occ_bits)
     feat, idx, wts = hash_encode(cfg, level_res, P["tables"], x)
     sh = sh_deg4(d[ray_id])
-    dec = relu_decisions(P, feat, sh, decide_in) if decide_in not in (None, "fp32") else None
-    fw = field_forward(P, feat, sh, dec)
+    fw = field_forward(P, feat, sh, bits_of(mlp_bits))
     delta = float(cfg.step)
     t64 = t.astype(np.float64)
     I_hat, D_hat, acc, w, Tcum = composite(ray_id, fw["sigma"], fw["rgb"], t64, delta, n_rays)
@@ -603,17 +613,17 @@ def render_rays_f32(c2w, K, W, H):
     return o, d
 
 
-def render(cfg, P, c2w, K, W, H, occ_bits=None, level_res=None, t_min=None, decide_in=None):
-    """Forward-only render of a W x H view (PAPER Sec. 3.3, the mapping thread also
+def render(cfg, P, c2w, K, W, H, occ_bits=None, level_res=None, t_min=None, mlp_bits=None):
+    """Forward-only render of a W x H view (Sec. 3.3, the mapping thread also
     renders): colour [H*W, 3] and expected depth [H*W]; with t_min, samples after
-    the transmittance drops below t_min are skipped."""
+    the transmittance drops below t_min are skipped.  mlp_bits as in
+    forward_backward."""
     level_res = level_resolutions(cfg) if level_res is None else level_res
     o, d = render_rays_f32(np.asarray(c2w, f32), np.asarray(K, f32), W, H)
     ray_id, _, t, x = march(cfg, o, d, occ_bits)
     feat, _, _ = hash_encode(cfg, level_res, P["tables"], x)
     sh = sh_deg4(d[ray_id])
-    dec = relu_decisions(P, feat, sh, decide_in) if decide_in not in (None, "fp32") else None
-    fw = field_forward(P, feat, sh, dec)
+    fw = field_forward(P, feat, sh, bits_of(mlp_bits))
     I_hat, D_hat, acc, _, _ = composite(ray_id, fw["sigma"], fw["rgb"], t.astype(np.float64),
                                         float(cfg.step), W * H, t_min)
     return I_hat, D_hat, acc
@@ -689,18 +699,17 @@ def hash_encode_dx(cfg, level_res, tables: np.ndarray, x: np.ndarray) -> np.ndar
     return out
 
 
-def pose_gradients(cfg, P, keyframes, n_rays, seed, step, occ_bits=None, level_res=None, decide_in=None):
+def pose_gradients(cfg, P, keyframes, n_rays, seed, step, occ_bits=None, level_res=None, mlp_bits=None):
     """Gradient of the batch loss with respect to each keyframe pose (left world-frame
     perturbation, see above) for the batch of forward_backward, its sample list held
     fixed.  Returns dict(loss, pose_grads [n_kf, 6] = (dL/drho, dL/dphi) per keyframe,
     g_o [R, 3], g_d [R, 3] per ray, kf [R])."""
     fb = forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits=occ_bits, level_res=level_res,
-                          decide_in=decide_in)
+                          mlp_bits=mlp_bits)
     lr = fb["level_res"]
     feat, _, _ = hash_encode(cfg, lr, P["tables"], fb["x"])
     sh = sh_deg4(fb["d"][fb["ray_id"]])
-    dec = relu_decisions(P, feat, sh, decide_in) if decide_in not in (None, "fp32") else None
-    fw = field_forward(P, feat, sh, dec)
+    fw = field_forward(P, feat, sh, bits_of(mlp_bits))
     _, dfeat, dsh = field_backward(P, fw, fb["dsigma"], fb["drgb"], with_dsh=True)
     dfdx = hash_encode_dx(cfg, lr, P["tables"], fb["x"])             # [S, E, 3]
     dLdx = np.einsum("se,sea->sa", dfeat, dfdx)                       # [S, 3]

@@ -119,6 +119,7 @@ _SIGS = {
                                            ctypes.c_size_t, ctypes.c_void_p]),
     "map_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MapStats)]),
     "map_abi_config_size": (ctypes.c_size_t, []),
+    "map_set_wait_polls": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "map_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
     "map_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "map_server_add_scene": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MapConfig), ctypes.c_int,
@@ -448,6 +449,10 @@ class NerfMap:
 
     def profile(self, enable: bool = True):
         self._check(self.lib.map_profile_enable(self.h, int(enable)))
+
+    def set_wait_polls(self, polls: int):
+        """Poll limit of the tensor-core kernels' MMA waits (0: expire at once)."""
+        self._check(self.lib.map_set_wait_polls(self.h, polls))
 
     def profile_read(self) -> dict:
         ms = np.zeros(8, np.float64)

@@ -207,6 +207,7 @@ void fill_devcfg(map_scene* h) {
     d.occ_res = c.occ_res;
     d.lambda_d = c.lambda_d;
     d.t_min = 0.f;
+    d.wait_polls = kWaitPollsDefault;
 }
 
 int copy_in(map_scene* h, void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_t s) {
@@ -736,7 +737,7 @@ int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, 
                                        cudaMemcpyDeviceToHost, s));
         NM_CUDA(h, cudaStreamSynchronize(s));  // the staging buffer is reused by the next chunk
     }
-    return MAP_OK;
+    return mem_kind == MAP_MEM_DEVICE ? MAP_OK : check_device_flags(h, s);
 }
 
 int map_get_params(map_handle h, float* dst, size_t n, int mem_kind, void* stream) {
@@ -908,6 +909,12 @@ int map_profile_read(map_handle h, double* ms, uint64_t* count, uint64_t* launch
         if (count) count[p] = cnt[p];
         if (launches) launches[p] = lch[p];
     }
+    return MAP_OK;
+}
+
+int map_set_wait_polls(map_handle h, uint32_t polls) {
+    if (!h) return MAP_EINVAL;
+    h->dc.wait_polls = polls;
     return MAP_OK;
 }
 

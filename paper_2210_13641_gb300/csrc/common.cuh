@@ -22,8 +22,12 @@ constexpr int kW3 = kHid * (kGeo + kSH);  // 2048
 constexpr int kW4 = kHid * kHid;          // 4096
 constexpr int kW5 = 3 * kHid;             // 192
 constexpr int kMlpParams = kW1 + kW2 + kW3 + kW4 + kW5;  // 9408
-// Density activation: sigma = exp(min(h_0, kSigmaHMax)), the truncated exponential of
-// Instant-NGP; beyond the cap a sample is opaque already and dsigma/dh_0 = 0.
+// Density activation: sigma = exp(min(h_0, kSigmaHMax)), an exponential whose value
+// is capped (a reading: the paper defers the activation to its map).  Beyond the cap
+// a sample is opaque already (sigma * delta > 10^4 at every spacing used here) and
+// sigma stays finite in FP32 through long fits; dsigma/dh_0 = 0 above it.  This is
+// not Instant-NGP's "truncated exponential", which leaves the value alone and clamps
+// the argument of the derivative instead.
 constexpr float kSigmaHMax = 15.f;
 constexpr int kOffW1 = 0, kOffW2 = kW1, kOffW3 = kW1 + kW2, kOffW4 = kOffW3 + kW3,
               kOffW5 = kOffW4 + kW4;
@@ -43,7 +47,12 @@ struct DevCfg {
     uint32_t occ_res;
     float lambda_d;
     float t_min;                  // render early-termination threshold (0: none)
+    uint32_t wait_polls;          // poll limit of each MMA-completion wait (tensor-core kernels)
 };
+
+// Default poll limit of a bounded MMA-completion wait: far beyond any MMA chain's
+// latency, far below a watchdog's reach.
+constexpr uint32_t kWaitPollsDefault = 1u << 24;
 
 // ----------------------------------------------------------------- exact FP32
 

@@ -38,7 +38,6 @@ using namespace tc;
 
 namespace {
 
-constexpr uint32_t kWaitPolls = 1u << 24;
 constexpr float kGradTarget = 256.f;  // largest scaled gradient seed (see above)
 
 // Two values rounded to the MLP type, a in the low half: one cvt to a packed pair
@@ -131,11 +130,23 @@ __device__ __forceinline__ void to_tensor() {
     fence_after_sync();
 }
 
-// Waits for the MMAs committed to `bar` (bounded); after a timeout the thread stops
-// waiting for the rest of the tile and the block leaves at the tile's end.
-__device__ __forceinline__ void wait_mma(uint64_t* bar, uint32_t& phase, bool& timed_out) {
-    if (!timed_out) timed_out = !mbar_wait(bar, phase, kWaitPolls);
+// Waits for the MMAs committed to `bar` (at most `polls` polls; 0 makes the wait
+// expire at once).  After a timeout the thread stops waiting, the rest of its work is
+// garbage, and the block drains its MMAs before it frees tensor memory (drain_mma).
+__device__ __forceinline__ void wait_mma(uint64_t* bar, uint32_t& phase, bool& timed_out, uint32_t polls) {
+    if (!timed_out) timed_out = !mbar_wait(bar, phase, polls);
     phase ^= 1u;
+    fence_after_sync();
+}
+
+// After a timeout: the MMA-issuing thread commits once more, to a barrier that has
+// seen no other commit, and waits for it (bounded by the default limit).  The commit
+// arrives when every MMA that thread has issued has completed, so the tensor memory
+// can be freed afterwards; the phases of the main barrier are not trusted (several
+// of its phases may have completed while nobody waited).
+__device__ __forceinline__ void drain_mma(uint64_t* drain_bar) {
+    mma_commit(drain_bar);
+    mbar_wait(drain_bar, 0u, kWaitPollsDefault);
     fence_after_sync();
 }
 
@@ -193,7 +204,7 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
                                                       uint4* __restrict__ feat_out, float feat_scale,
                                                       uint32_t* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t bar;
+    __shared__ uint64_t bar, drain_bar;
     __shared__ uint32_t tslot;
     uint8_t* sW1 = smem;
     uint8_t* sW2 = sW1 + kW1B;
@@ -209,6 +220,7 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
     if (warp == 0) tmem_alloc(&tslot, 64);
     if (tid == 0) {
         mbar_init(&bar, 1);
+        mbar_init(&drain_bar, 1);
         mbar_fence_init();
     }
     to_tensor();
@@ -253,7 +265,7 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
             gemm(tmem, kmaj(tA, 128), kmaj(sW1, 64), 2, idesc_f16(128, 64, BF16, false, false), false);
             mma_commit(&bar);
         }
-        wait_mma(&bar, phase, timed_out);
+        wait_mma(&bar, phase, timed_out, c.wait_polls);
 #pragma unroll
         for (int h = 0; h < 64; h += 32) {  // 32-column halves keep fewer values live
             ld_cols<32>(trow, h, v);
@@ -267,7 +279,7 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
             gemm(tmem, kmaj(tB, 128), kmaj(sW2, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
             mma_commit(&bar);
         }
-        wait_mma(&bar, phase, timed_out);
+        wait_mma(&bar, phase, timed_out, c.wait_polls);
         ld_cols<16>(trow, 0, v);
         const float sigma = expf(fminf(v[0], kSigmaHMax));
         if (valid) sh16(d.x, d.y, d.z, v + kGeo);
@@ -282,7 +294,7 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
             gemm(tmem, kmaj(tA, 128), kmaj(sW3, 64), 2, idesc_f16(128, 64, BF16, false, false), false);
             mma_commit(&bar);
         }
-        wait_mma(&bar, phase, timed_out);
+        wait_mma(&bar, phase, timed_out, c.wait_polls);
 #pragma unroll
         for (int h = 0; h < 64; h += 32) {
             ld_cols<32>(trow, h, v);
@@ -294,7 +306,7 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
             gemm(tmem, kmaj(tB, 128), kmaj(sW4, 64), 4, idesc_f16(128, 64, BF16, false, false), false);
             mma_commit(&bar);
         }
-        wait_mma(&bar, phase, timed_out);
+        wait_mma(&bar, phase, timed_out, c.wait_polls);
 #pragma unroll
         for (int h = 0; h < 64; h += 32) {
             ld_cols<32>(trow, h, v);
@@ -306,7 +318,7 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
             gemm(tmem, kmaj(tB, 128), kmaj(sW5, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
             mma_commit(&bar);
         }
-        wait_mma(&bar, phase, timed_out);
+        wait_mma(&bar, phase, timed_out, c.wait_polls);
         ld_cols<16>(trow, 0, v);
         if (valid) sig_rgb[i] = make_float4(sigma, sigmoidf_(v[0]), sigmoidf_(v[1]), sigmoidf_(v[2]));
         fence_before_sync();
@@ -316,9 +328,14 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
         }
     }
     fence_before_sync();
-    __syncthreads();
+    const bool any_timeout = __syncthreads_or(timed_out) != 0;
     fence_after_sync();
-    if (timed_out) mbar_wait(&bar, phase ^ 1u, kWaitPolls);
+    if (any_timeout) {
+        if (tid == 0) drain_mma(&drain_bar);
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+    }
     if (warp == 0) tmem_dealloc(tmem, 64);
 }
 
@@ -413,7 +430,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                                                          const float* __restrict__ seed_max,
                                                          float4* __restrict__ pose_s, uint32_t* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t bar;
+    __shared__ uint64_t bar, drain_bar;
     __shared__ uint32_t tslot;
     uint8_t* sW1 = smem;
     uint8_t* sW2 = sW1 + kW1B;
@@ -434,6 +451,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
     if (warp == 0) tmem_alloc(&tslot, 256);
     if (tid == 0) {
         mbar_init(&bar, 1);
+        mbar_init(&drain_bar, 1);
         mbar_fence_init();
     }
     to_tensor();
@@ -468,14 +486,14 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 gemm(tmem, kmaj(tX0, 128), kmaj(sW1, 64), 2, kM128N64, false);
                 mma_commit(&bar);
             }
-            wait_mma(&bar, phase, timed_out);
+            wait_mma(&bar, phase, timed_out, c.wait_polls);
             relu_epilogue<BF16>(trow, tH1, r, inv_fs, m1a, m1b);
             to_tensor_mlp();
             if (r == 0) {
                 gemm(tmem, kmaj(tH1, 128), kmaj(sW2, 16), 4, kM128N16, false);
                 mma_commit(&bar);
             }
-            wait_mma(&bar, phase, timed_out);
+            wait_mma(&bar, phase, timed_out, c.wait_polls);
             float y[32];
             ld_cols<16>(trow, 0, y);
             const float sigma = expf(fminf(y[0], kSigmaHMax));
@@ -491,14 +509,14 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 gemm(tmem, kmaj(tX3, 128), kmaj(sW3, 64), 2, kM128N64, false);
                 mma_commit(&bar);
             }
-            wait_mma(&bar, phase, timed_out);
+            wait_mma(&bar, phase, timed_out, c.wait_polls);
             relu_epilogue<BF16>(trow, tH3, r, 1.f, m3a, m3b);
             to_tensor_mlp();
             if (r == 0) {
                 gemm(tmem, kmaj(tH3, 128), kmaj(sW4, 64), 4, kM128N64, false);
                 mma_commit(&bar);
             }
-            wait_mma(&bar, phase, timed_out);
+            wait_mma(&bar, phase, timed_out, c.wait_polls);
             relu_epilogue<BF16>(trow, tH4, r, 1.f, m4a, m4b);
             // the colours' gradient seed dz (FP32, scaled by S) comes from the IO group
             v[0] = rz.x;
@@ -514,7 +532,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 gemm(tmem, kmaj(tG5, 128), mnmaj(sW5, 16), 1, idesc_f16(128, 64, BF16, false, true), false);
                 mma_commit(&bar);
             }
-            wait_mma(&bar, phase, timed_out);
+            wait_mma(&bar, phase, timed_out, c.wait_polls);
             mask_epilogue<BF16>(trow, tH4, r, m4a, m4b);                 // G4
             // dW4 += G4^T H3 ; dH3 = G4 W4
             to_tensor_mlp();
@@ -523,7 +541,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 gemm(tmem, kmaj(tH4, 128), mnmaj(sW4, 64), 4, idesc_f16(128, 64, BF16, false, true), false);
                 mma_commit(&bar);
             }
-            wait_mma(&bar, phase, timed_out);
+            wait_mma(&bar, phase, timed_out, c.wait_polls);
             mask_epilogue<BF16>(trow, tH3, r, m3a, m3b);                 // G3
             // dW3 += G3^T X3 ; dX3 = G3 W3
             to_tensor_mlp();
@@ -532,7 +550,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 gemm(tmem, kmaj(tH3, 128), mnmaj(sW3, 64), 4, idesc_f16(128, 32, BF16, false, true), false);
                 mma_commit(&bar);
             }
-            wait_mma(&bar, phase, timed_out);
+            wait_mma(&bar, phase, timed_out, c.wait_polls);
             if (kPose) {
                 // the SH inputs' gradient (columns 16..31, colour scale) -> view direction
                 ld_cols<16>(trow, 16, v);
@@ -555,7 +573,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 gemm(tmem, kmaj(tX3, 128), mnmaj(sW2, 16), 1, idesc_f16(128, 64, BF16, false, true), false);
                 mma_commit(&bar);
             }
-            wait_mma(&bar, phase, timed_out);
+            wait_mma(&bar, phase, timed_out, c.wait_polls);
             mask_epilogue<BF16>(trow, tH1, r, m1a, m1b);                 // G1
             // dW1 += G1^T X0 ; dF = G1 W1
             to_tensor_mlp();
@@ -564,7 +582,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 gemm(tmem, kmaj(tH1, 128), mnmaj(sW1, 64), 4, idesc_f16(128, 32, BF16, false, true), false);
                 mma_commit(&bar);
             }
-            wait_mma(&bar, phase, timed_out);
+            wait_mma(&bar, phase, timed_out, c.wait_polls);
             ld_cols<32>(trow, 0, v);
             fence_before_sync();
             if (k > 0) nb_sync(kBarDfFree, 256);          // the IO group has read the previous tile's rows
@@ -577,7 +595,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
         // ---- flush the weight gradients (lane 32*(m/16) + m%16 holds row m)
         const bool any_timeout = __syncthreads_or(timed_out) != 0;  // both groups take part
         fence_after_sync();
-        if (timed_out) mbar_wait(&bar, phase ^ 1u, kWaitPolls);
+        if (any_timeout && r == 0) drain_mma(&drain_bar);          // r == 0 issued every MMA
         if (n_mine > 0 && !any_timeout) {
             float* gm_ = grads + (size_t)c.L * c.T * 2;
             const int lane = tid & 31;

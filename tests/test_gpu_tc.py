@@ -1,17 +1,19 @@
 """Parity of the tensor-core (FP16 / BF16 MLP) mapping path with the FP64 oracle.
 
-The oracle takes each ReLU branch in the MLP's precision (a branch is an integer
-decided by floating point; oracle.relu_decisions) and computes every value in FP64.
+Two oracles.  The rounding model (oracle mlp_bits: every MLP operand rounded to the
+format's 11 or 8 significant bits, products summed exactly) is the FP64 oracle of
+an MLP whose operands are FP16 / BF16, which the precision pattern prescribes; the
+plain oracle is the unrounded FP64 chain.
 
-Tolerances: loss within 2e-3 relative; per-ray colour, depth and opacity within
-2e-3 relative plus 2e-3 absolute; every gradient tensor within 2e-3 relative in L2
-norm for FP16.  BF16 gradients are held to 4 units of BF16 roundoff (4 * 2^-9 =
-7.8e-3): with 8 significand bits, rounding the weights or the activations alone
-already moves the weight gradients by about 2e-3 against FP64 (an FP64 emulation of
-the rounding shows this), so 2e-3 is below what any BF16 MLP reaches.  Sample
-lists are bit-exact (they do not depend on the MLP).  When NERFMAP_PRECISION_REPORT
-names a file, the measured errors (against this oracle and against the plain FP64
-oracle whose ReLU branches follow FP64 signs) are appended to it as JSON lines.
+Tolerances: against the rounding model, the benchmark spec's 2e-3 relative on the loss,
+on per-ray colour, depth and opacity (plus 2e-3 absolute) and on every gradient
+tensor (relative L2), in both formats.  Against the plain oracle, every gradient
+tensor within 2e-3 plus the rounding model's own distance from the plain oracle on
+the same inputs (the floor no FP16 / BF16 MLP can go below: a pre-activation within
+a rounding of zero takes the other ReLU branch; test_oracle_pins pins that floor
+above 2e-3 on the C1 step), and the loss within 2e-3.  Sample lists are bit-exact
+(they do not depend on the MLP).  When NERFMAP_PRECISION_REPORT names a file, the
+measured errors are appended to it as JSON lines.
 """
 
 import json
@@ -26,7 +28,6 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TOL = 2e-3
-GRAD_TOL = {"fp16": 2e-3, "bf16": 4 * 2.0 ** -9}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,7 +65,7 @@ def _report(case, prec, errs):
 def _step_case(name, cfg, P, kfs, n, seed, bits=None):
     m = _map(cfg, P, kfs, bits)
     loss = m.step(n, seed=seed, no_update=True)
-    ref = oracle.forward_backward(cfg, P, kfs, n, seed, 0, occ_bits=bits, decide_in=cfg.precision)
+    ref = oracle.forward_backward(cfg, P, kfs, n, seed, 0, occ_bits=bits, mlp_bits=cfg.precision)
     plain = oracle.forward_backward(cfg, P, kfs, n, seed, 0, occ_bits=bits)
     rid, t = m.samples()
     assert np.array_equal(rid, ref["ray_id"].astype(np.uint32)) and np.array_equal(t, ref["t"])
@@ -76,14 +77,16 @@ def _step_case(name, cfg, P, kfs, n, seed, bits=None):
     for k in ("tables", "W1", "W2", "W3", "W4", "W5"):
         errs["grad_" + k] = _rel(G[k], ref["grads"][k])
         errs["plain_grad_" + k] = _rel(G[k], plain["grads"][k])
+        errs["floor_grad_" + k] = _rel(ref["grads"][k], plain["grads"][k])
     errs["plain_loss"] = abs(loss - plain["loss"]) / abs(plain["loss"])
     _report(name, cfg.precision, errs)
-    assert errs["loss"] <= TOL, errs
+    assert errs["loss"] <= TOL and errs["plain_loss"] <= TOL, errs
     assert np.allclose(rgb, ref["I_hat"], rtol=TOL, atol=TOL)
     assert np.allclose(D, ref["D_hat"], rtol=TOL, atol=TOL)
     assert np.allclose(acc, ref["acc"], rtol=TOL, atol=TOL)
     for k in ("tables", "W1", "W2", "W3", "W4", "W5"):
-        assert errs["grad_" + k] <= GRAD_TOL[cfg.precision], (k, errs)
+        assert errs["grad_" + k] <= TOL, (k, errs)
+        assert errs["plain_grad_" + k] <= TOL + errs["floor_grad_" + k], (k, errs)
     return m
 
 
@@ -117,7 +120,7 @@ def test_render_tensor_cores(prec):
     kf = synth.c1_keyframe(9, W=40, H=30)
     rgb, D, acc = m.render(kf.c2w, kf.K, 40, 30)
     I_ref, D_ref, A_ref = oracle.render(cfg, P, kf.c2w, kf.K, 40, 30, t_min=float(cfg.render_t_min),
-                                        decide_in=prec)
+                                        mlp_bits=prec)
     errs = {"rgb_max_abs": float(np.abs(rgb.reshape(-1, 3) - I_ref).max()),
             "depth_rel": _rel(D.ravel(), D_ref), "acc_max_abs": float(np.abs(acc.ravel() - A_ref).max())}
     _report("render_small", prec, errs)
