@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--no-serving", action="store_true", help="skip the multi-scene serving measurement")
     p.add_argument("--no-large-map", action="store_true", help="skip the large-map precision comparison")
     p.add_argument("--large-map-keyframes", type=int, default=2000)
+    p.add_argument("--large-map-rays", type=int, default=1 << 20)
+    p.add_argument("--large-map-precisions", default="bf16,fp16,fp32")
+    p.add_argument("--only-large-map", action="store_true",
+                   help="run only the large-map leg (reduced sizes for profiler captures) and print its JSON")
     p.add_argument("--ablation", action="store_true", help="also run the Sigma_D-weighting ablation (about 1 min)")
     p.add_argument("--serving-seconds", type=float, default=6.0)
     p.add_argument("--rays", type=int, default=N_RAYS)
@@ -89,13 +93,17 @@ def oracle_steps(cfg, kfs, bits, params, n_sample, n_steps, seed=0):
 
 
 def cpu_baseline_child(args):
+    os.environ.update(ONE_THREAD)
     cfg, kfs, bits, params = make_workload("fp32")
     times = oracle_steps(cfg, kfs, bits, params, args.sample_rays, 1)
     print(json.dumps({"value": args.sample_rays / times[0], "seconds": times[0]}))
 
 
+ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
 def run_cpu_baseline(sample_rays: int):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env = dict(os.environ, **ONE_THREAD)
     p = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only",
                         "--sample-rays", str(sample_rays)], env=env, capture_output=True, text=True,
                        timeout=900)
@@ -104,7 +112,8 @@ def run_cpu_baseline(sample_rays: int):
     r = json.loads(p.stdout.strip().splitlines()[-1])
     return {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{sample_rays} rays of the workload, one fwd+bwd+Adam step in FP64 numpy "
-                      f"({r['seconds']:.1f} s; Adam over all parameters)"}
+                      f"({r['seconds']:.1f} s; Adam over all parameters; one thread: BLAS/OpenMP "
+                      f"threads pinned to 1)"}
 
 
 def max_over_ranks(dist, x, device="cuda"):
@@ -133,14 +142,14 @@ def run_reference(args, rank, world):
     times = oracle_steps(cfg, kfs, bits, params, n, args.steps)
     tot = sum(times)
     value = n * args.steps / tot
-    cores = 1 if os.environ.get("OPENBLAS_NUM_THREADS") == "1" else os.cpu_count()
+    cores = 1  # main() pins the BLAS / OpenMP threads to one before numpy loads
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "rays_per_step": n,
                                             "note": "FP64 CPU oracle, bounded sample of each step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{n} rays per step of the workload"},
+                             "sample": f"{n} rays per step of the workload, one thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -485,6 +494,97 @@ NCU_TRAFFIC = {
 }
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+_L2 = {}
+
+
+def l2_ceilings(cfg):
+    """Measured ceilings for the table traffic (benchmark-only probe library): the
+    streaming L2 bandwidth of 16-byte reads and of 16-byte FP32 vector reductions
+    over a buffer the size of the workload's tables, and the uniformly random
+    8-byte read / reduction rates into a table of that size."""
+    key = (cfg.n_levels, cfg.log2_table)
+    if key not in _L2:
+        import torch
+        from paper_2210_13641_gb300 import probe
+        mb = (cfg.n_levels << cfg.log2_table) * 8 / 2 ** 20
+        tab = torch.zeros((cfg.n_levels << cfg.log2_table, 2), device="cuda")
+        _L2[key] = {"buffer_mb": mb,
+                    "stream_read_gbs": probe.l2_stream(mb, 0)["payload_gbs"],
+                    "stream_reduce_gbs": probe.l2_stream(mb, 1)["payload_gbs"],
+                    "random_read_gbs": probe.random_access(tab, per_thread=64, mode=0)["payload_gbs"],
+                    "random_reduce_gbs": probe.random_access(tab, per_thread=64, mode=1)["payload_gbs"],
+                    "source": "measured in this run: probe/k_probe.cu (streaming sweeps of a buffer the size "
+                              "of the tables; uniformly random 8-byte accesses into a table of that size)"}
+        del tab
+    return _L2[key]
+
+
+def roofline(cfg, prof, n_samples, n_params, precision):
+    """Roofline of the step's dominant kernel.  The tables (64 MB at the room
+    workload) stay in the L2, so the table traffic's bound is the L2: the forward's
+    gathers are set against the L2's streaming read bandwidth, the backward's
+    reductions against its streaming reduction bandwidth (both measured here over a
+    buffer the size of the tables); achieved = the table's algorithmic bytes
+    (8 corners x L levels x F features x 4 B per sample, read or reduced) / the
+    kernel's CUDA-event time.  The per-sample streams (ray data, the stored encoding,
+    colours and their gradients) go to HBM; the HBM line reports the ncu DRAM bytes
+    of the kernel against the measured copy bandwidth."""
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ab = algorithmic_bytes(cfg, n_samples, n_params)
+    cand = {k: prof[k]["ms"] / max(prof[k]["count"], 1) for k in ("field_fwd", "field_bwd", "adam")}
+    dom = max(cand, key=cand.get)
+    l2 = l2_ceilings(cfg)
+    table_bytes = n_samples * 8 * cfg.n_levels * cfg.n_features * 4
+    kernels = {}
+    for k, peak_key in (("field_fwd", "stream_read_gbs"), ("field_bwd", "stream_reduce_gbs")):
+        ach = table_bytes / (cand[k] / 1e3) / 1e9
+        tr = measured_traffic(k, precision, n_samples)
+        kernels[k] = {"bound": "l2", "achieved": ach, "peak": l2[peak_key], "unit": "GB/s",
+                      "frac": ach / l2[peak_key], "ms": cand[k],
+                      "frac_of_random_ceiling": ach / l2["random_read_gbs" if k == "field_fwd" else "random_reduce_gbs"],
+                      "hbm": {"traffic": tr, "achieved": None if tr is None else tr / (cand[k] / 1e3) / 1e9,
+                              "peak": hbm, "frac": None if tr is None else tr / (cand[k] / 1e3) / 1e9 / hbm}}
+    adam_gbs = ab["adam"] / (cand["adam"] / 1e3) / 1e9
+    kernels["adam"] = {"bound": "hbm", "achieved": adam_gbs, "peak": hbm, "unit": "GB/s", "frac": adam_gbs / hbm,
+                       "ms": cand["adam"]}
+    d = kernels[dom]
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "GB/s",
+            "frac": d["frac"], "traffic": measured_traffic(dom, precision, n_samples),
+            "bytes_per_sample": 8 * cfg.n_levels * cfg.n_features * 4,
+            "peak_source": ("L2 streaming " + ("reductions" if dom == "field_bwd" else "reads") +
+                            " over a buffer the size of the tables, measured in this run" if dom != "adam"
+                            else ("measured" if "hbm_gbs" in peaks else "fallback") + " HBM copy bandwidth"),
+            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, scaled to this "
+                            "launch's samples; the tables stay in L2, so DRAM traffic is the per-sample streams",
+            "l2_ceilings": l2, "kernels": kernels,
+            "tensor_pipe_active": measured_tensor_pipe(precision),
+            "phase_ms_per_step": {k: v["ms"] / max(v["count"], 1) for k, v in prof.items() if v["count"]}}
+    return roof
+
+
+def render_roofline(cfg, rprof, n_views, samples_per_view, pixels, ms_per_view, precision):
+    """Roofline of a render: its forward field kernel gathers 8 corners x L levels
+    x F features x 4 B per retained sample (early termination is applied in the
+    compositing, after the forward), against the L2 streaming read bandwidth."""
+    l2 = l2_ceilings(cfg)
+    fwd_ms = rprof["field_fwd"]["ms"] / n_views
+    table_bytes = samples_per_view * 8 * cfg.n_levels * cfg.n_features * 4
+    ach = table_bytes / (fwd_ms / 1e3) / 1e9
+    return {"kernel": "field_fwd", "bound": "l2", "achieved": ach, "peak": l2["stream_read_gbs"], "unit": "GB/s",
+            "frac": ach / l2["stream_read_gbs"], "ms_per_view": ms_per_view, "field_fwd_ms_per_view": fwd_ms,
+            "samples_per_pixel": samples_per_view / pixels, "pixels": pixels,
+            "phase_ms_per_view": {k: v["ms"] / n_views for k, v in rprof.items() if v["count"]}}
+
+
 def kernel_sources_digest():
     import hashlib
     h = hashlib.sha256()
@@ -526,7 +626,18 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
+        os.environ.update(ONE_THREAD)                  # before numpy is first imported
         run_reference(args, rank, world)
+        return
+
+    if args.only_large_map:
+        import torch
+        torch.cuda.set_device(local)
+        import __graft_entry__
+        __graft_entry__.build()
+        out = large_map_benchmark(n_kf=args.large_map_keyframes, rays=args.large_map_rays, steps=args.steps,
+                                  warmup=args.warmup, precisions=tuple(args.large_map_precisions.split(",")))
+        print(json.dumps({"large_map": out}), flush=True)
         return
 
     cpu = None
@@ -586,37 +697,7 @@ def main():
     value = replica_throughput(n * args.steps, world, ms / 1e3)
 
     # ---------------- roofline of the dominant kernel (phase times inside the timed region)
-    import json as _json
-    peaks = {}
-    try:
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    ab = algorithmic_bytes(cfg, n_samples, m.n_params)
-    cand = {k: prof[k]["ms"] / max(prof[k]["count"], 1) for k in ("field_fwd", "field_bwd", "adam")}
-    dom = max(cand, key=cand.get)
-    achieved = ab[dom] / (cand[dom] / 1e3) / 1e9
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": measured_traffic(dom, args.precision, n_samples),
-            "tensor_pipe_active": measured_tensor_pipe(args.precision),
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "phase_ms_per_step": {k: v["ms"] / max(v["count"], 1) for k, v in prof.items() if v["count"]}}
-    # the tables are L2-resident: also compare the table traffic with the measured
-    # random-access ceiling for a table of this size (uniform 8-byte reads / reductions)
-    from paper_2210_13641_gb300 import binding as _b
-    tab = torch.zeros((cfg.n_levels << cfg.log2_table, 2), device="cuda")
-    g = _b.probe_random_access(tab, per_thread=64, mode=0)
-    a = _b.probe_random_access(tab, per_thread=64, mode=1)
-    del tab
-    table_bytes = n_samples * 8 * cfg.n_levels * cfg.n_features * 4
-    fwd_gbs = table_bytes / (cand["field_fwd"] / 1e3) / 1e9
-    bwd_gbs = table_bytes / (cand["field_bwd"] / 1e3) / 1e9
-    roof["random_access_ceiling"] = {
-        "table_mb": (cfg.n_levels << cfg.log2_table) * 8 / 2 ** 20,
-        "gather_gbs": g["payload_gbs"], "atomic_gbs": a["payload_gbs"],
-        "field_fwd_table_gbs": fwd_gbs, "field_fwd_frac_of_gather": fwd_gbs / g["payload_gbs"],
-        "field_bwd_table_gbs": bwd_gbs, "field_bwd_frac_of_atomic": bwd_gbs / a["payload_gbs"]}
+    roof = roofline(cfg, prof, n_samples, m.n_params, args.precision)
 
     # ---------------- end to end: keyframe upload from pinned host memory + step + loss read
     pinned = []
@@ -647,16 +728,48 @@ def main():
     for i in range(3):
         m.render(kfs[i].c2w, kfs[i].K, W, H, out_rgb=out, out_depth=dep, stream=stream)
     torch.cuda.synchronize()
+    nv = max(args.steps, 5)
+    render_samples = 0
+    for i in range(nv):                                   # retained samples of each timed view
+        k = kfs[i % len(kfs)]
+        m.render(k.c2w, k.K, W, H, out_rgb=out, out_depth=dep, stream=stream)
+        render_samples += m.stats().render_samples
+    m.profile(True)
     r0 = torch.cuda.Event(enable_timing=True)
     r1 = torch.cuda.Event(enable_timing=True)
     r0.record(stream)
-    nv = max(args.steps, 5)
     for i in range(nv):
         k = kfs[i % len(kfs)]
         m.render(k.c2w, k.K, W, H, out_rgb=out, out_depth=dep, stream=stream)
     r1.record(stream)
     torch.cuda.synchronize()
-    render_mpx = W * H * nv / (r0.elapsed_time(r1) / 1e3) / 1e6 * world
+    rprof = m.profile_read()
+    m.profile(False)
+    render_ms = r0.elapsed_time(r1) / nv
+    render_mpx = W * H / (render_ms / 1e3) / 1e6 * world
+    render = render_roofline(cfg, rprof, nv, render_samples / nv, W * H, render_ms, args.precision)
+    render["value"] = render_mpx
+    render["unit"] = "Mpx/s"
+
+    # ---------------- occupancy refresh (a13, every 16 steps in a mapping run): its cost
+    # per refresh and amortised over 16 steps, beside the headline step
+    torch.cuda.synchronize()
+    m.refresh_occupancy(stream=stream)                    # warm
+    torch.cuda.synchronize()
+    o0 = torch.cuda.Event(enable_timing=True)
+    o1 = torch.cuda.Event(enable_timing=True)
+    o0.record(stream)
+    for _ in range(3):
+        m.refresh_occupancy(stream=stream)
+    o1.record(stream)
+    torch.cuda.synchronize()
+    occ_ms = o0.elapsed_time(o1) / 3
+    step_ms = ms / args.steps
+    occupancy = {"cells": cfg.occ_res ** 3, "ms_per_refresh": occ_ms, "refresh_every": 16,
+                 "amortised_ms_per_step": occ_ms / 16,
+                 "rays_per_s_with_refresh": n / ((step_ms + occ_ms / 16) / 1e3) * world,
+                 "note": "one density evaluation (encoding + density MLP, FP32) per cell at a jittered point, "
+                         "EMA and threshold; timed after the timed steps, outside them"}
 
     # ---------------- the other MLP precisions on the same workload (FP32 plain form, BF16)
     m.close()
@@ -693,7 +806,8 @@ def main():
         serving = {p: serving_benchmark(p, kfs, bits, args.serving_seconds) for p in (args.precision, "fp32")}
     large = None
     if not args.no_large_map and rank == 0:
-        large = large_map_benchmark(n_kf=args.large_map_keyframes)
+        large = large_map_benchmark(n_kf=args.large_map_keyframes, rays=args.large_map_rays,
+                                    precisions=tuple(args.large_map_precisions.split(",")))
     ablation = sigma_d_ablation(args.precision) if args.ablation and rank == 0 else None
     cov = covariance_benchmark() if rank == 0 and not args.no_large_map else None
 
@@ -707,8 +821,8 @@ def main():
                            "samples_per_step": n_samples, "mean_samples_per_ray": n_samples / n,
                            "l2": "working set > L2: params+grads+Adam moments (0.27 GB) streamed every step",
                            "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
-                "roofline": roof, "render_mpx_s": render_mpx, "e2e": e2e, "clocks": clk,
-                "gpu_launches": int(launches), "forms": forms}
+                "roofline": roof, "render_mpx_s": render_mpx, "render": render, "occupancy_refresh": occupancy,
+                "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "forms": forms}
         if serving:
             line["serving"] = serving
         if large:

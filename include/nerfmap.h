@@ -129,6 +129,7 @@ typedef struct map_stats {
     uint64_t param_count;   /* FP32 parameters (tables then MLP weights) */
     uint64_t device_bytes;  /* device memory held by the map */
     uint64_t kernel_launches; /* kernels this map has launched since creation */
+    uint64_t render_samples;  /* retained samples of the last map_render, all its chunks */
 } map_stats;
 
 /* Phases of a step or render, for map_profile_read. */
@@ -360,17 +361,6 @@ int map_profile_read(map_handle h, double* ms, uint64_t* count, uint64_t* launch
 int map_march_noalloc(const map_config* cfg, const uint8_t* occ_bits, const float* rays_o,
                       const float* rays_d, uint32_t n_rays, uint32_t* offsets, uint32_t* ray_id,
                       float* t, size_t cap_samples, void* stream);
-
-/*
- * map_probe_random_access - measurement kernel (no counterpart in the paper): the
- * ceiling for the hash-grid traffic.  n_threads threads each make per_thread
- * accesses to uniformly random entries of `table` (device, n_entries float2 pairs,
- * n_entries a power of two): mode 0 reads them (8 bytes each), mode 1 adds
- * (1e-30, 1e-30) to them with FP32 vector reductions.  sink: device, 2 floats.
- * Queued on `stream`; the caller times it.  Returns MAP_EINVAL on bad arguments.
- */
-int map_probe_random_access(float* table, uint64_t n_entries, uint32_t n_threads, uint32_t per_thread,
-                            int mode, uint64_t seed, float* sink, void* stream);
 
 /*
  * Serving: several maps resident on one GPU (Sec. 3.3's mapping thread, which

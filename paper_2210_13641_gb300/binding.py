@@ -53,7 +53,8 @@ class MapConfig(ctypes.Structure):
 class MapStats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_uint64), ("n_samples", ctypes.c_uint64), ("n_rays", ctypes.c_uint32),
                 ("n_keyframes", ctypes.c_uint32), ("param_count", ctypes.c_uint64),
-                ("device_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+                ("device_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("render_samples", ctypes.c_uint64)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -137,8 +138,6 @@ _SIGS = {
     "map_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                                        ctypes.POINTER(ctypes.c_uint32)]),
     "map_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
-    "map_probe_random_access": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                                               ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "map_march_noalloc": (ctypes.c_int, [ctypes.POINTER(MapConfig), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -152,33 +151,6 @@ _lib = None
 
 def exported_symbols() -> list:
     return list(_SIGS)
-
-
-def probe_random_access(table, per_thread: int, mode: int, n_threads: int = 152 * 2048, seed: int = 1,
-                        reps: int = 5) -> dict:
-    """Times map_probe_random_access on a CUDA float32 tensor `table` ([n, 2], n a
-    power of two): returns accesses/s and 8-byte payload GB/s (best of `reps`)."""
-    import torch
-    lib = load()
-    sink = torch.zeros(2, device=table.device)
-    s = torch.cuda.current_stream()
-    n = table.numel() // 2
-    best = None
-    for r in range(reps + 1):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        rc = lib.map_probe_random_access(table.data_ptr(), n, n_threads, per_thread, mode, seed + r,
-                                         sink.data_ptr(), s.cuda_stream)
-        e1.record(s)
-        if rc != MAP_OK:
-            raise MapError(rc, "probe failed")
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if r > 0 and (best is None or ms < best):
-            best = ms
-    acc = n_threads * per_thread
-    return {"accesses_per_s": acc / (best / 1e3), "payload_gbs": acc * 8 / (best / 1e3) / 1e9, "ms": best}
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:

@@ -81,6 +81,27 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False, ptxas
     return LIB
 
 
+PROBE_DIR = os.path.join(HERE, "probe")
+PROBE_LIB = os.path.join(HERE, "libnerfmap_probe.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """Compile the benchmark's measurement kernels (probe/*.cu) into
+    libnerfmap_probe.so, a library of its own outside the mapping ABI."""
+    srcs = sorted(os.path.join(PROBE_DIR, f) for f in os.listdir(PROBE_DIR) if f.endswith(".cu"))
+    if not force and os.path.exists(PROBE_LIB) and all(os.path.getmtime(s) <= os.path.getmtime(PROBE_LIB)
+                                                       for s in srcs + [os.path.abspath(__file__)]):
+        return PROBE_LIB
+    tmp = PROBE_LIB + ".tmp"
+    cmd = [_nvcc(), ARCH, "-std=c++17", "-lineinfo", "-O3", "-Xcompiler", "-fPIC", "-shared", *srcs, "-o", tmp]
+    p = subprocess.run(cmd, capture_output=True, text=True)
+    if p.returncode != 0:
+        raise RuntimeError(f"nvcc failed on the probe library:\n{p.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv))
+    print(build_probe(force="--force" in sys.argv))

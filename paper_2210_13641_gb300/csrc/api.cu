@@ -708,6 +708,7 @@ int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, 
     DevCfg dc = h->dc;
     dc.t_min = h->cfg.render_t_min;
     float* tmp = b.feat;  // host outputs: staged here (unused by a render), then copied
+    NM_CUDA(h, cudaMemsetAsync(render_sample_counter(b), 0, sizeof(unsigned long long), s));
     for (uint32_t p0 = 0; p0 < n; p0 += chunk) {
         const uint32_t cnt = std::min(chunk, n - p0);
         rc = phase(h, MAP_PH_RAYGEN, 1, s, [&] { launch_ray_gen_view(c2w, K, W, p0, cnt, b, s); });
@@ -879,7 +880,10 @@ int map_get_stats(map_handle h, map_stats* out) {
     out->param_count = h->n_params;
     out->device_bytes = h->held;
     out->kernel_launches = h->launches;
-    return MAP_OK;
+    unsigned long long rs = 0;
+    if (h->bufs.loss) rc = copy_out(h, &rs, render_sample_counter(h->bufs), sizeof(rs), MAP_MEM_HOST, h->last_stream);
+    out->render_samples = rs;
+    return rc;
 }
 
 int map_profile_enable(map_handle h, int enable) {

@@ -48,12 +48,17 @@ struct StepBufs {
     float4* dsig_rgb;       // [cap_samples] dL/dsigma, dL/dr, dL/dg, dL/db (w_i while compositing)
     float* feat;            // [cap_samples][32] stored encodings (FP32)
     float* ray_out;         // [5][cap_rays] I*r, I*g, I*b, D*, acc
-    float* loss;            // [0] batch loss, [1] [2] largest seeds (FP32 bits), [3] block counter
+    float* loss;            // [0] batch loss, [1] [2] largest seeds (FP32 bits), [3] block counter,
+                            // bytes 32..39: retained samples of the current render (all chunks)
     float* partials;        // [kCompositeMaxBlocks][4] per-block sums of the compositing kernel
     float4* pose_s;         // [cap_samples][2] per-sample pose terms (dL/dp, dL/dd via SH); lazily
     uint32_t* err;          // [1]
     uint64_t cap_samples;
 };
+
+inline unsigned long long* render_sample_counter(const StepBufs& b) {
+    return reinterpret_cast<unsigned long long*>(b.loss + 8);
+}
 
 // k_rays.cu
 void launch_set_kf_desc(KfDesc* table, uint32_t idx, const KfDesc& d, cudaStream_t s);

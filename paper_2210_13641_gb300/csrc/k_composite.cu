@@ -227,10 +227,14 @@ void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const Ste
 namespace nm {
 
 // Render output: per-ray planes -> interleaved RGB [n][3], depth [n], opacity [n].
+// Also adds the chunk's retained sample count (offsets[n] of the march's scan) to the
+// render's running total.
 __global__ void k_write_render(const float* __restrict__ ray_out, uint32_t cap, uint32_t n,
                                float* __restrict__ rgb, float* __restrict__ depth,
-                               float* __restrict__ acc) {
+                               float* __restrict__ acc, const uint32_t* __restrict__ chunk_total,
+                               unsigned long long* __restrict__ render_samples) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) atomicAdd(render_samples, (unsigned long long)*chunk_total);
     if (r >= n) return;
     if (rgb) {
         rgb[3 * r] = ray_out[r];
@@ -243,7 +247,8 @@ __global__ void k_write_render(const float* __restrict__ ray_out, uint32_t cap, 
 
 void launch_write_render(const StepBufs& b, uint32_t n, float* rgb, float* depth, float* acc,
                          cudaStream_t s) {
-    k_write_render<<<(n + 255) / 256, 256, 0, s>>>(b.ray_out, b.cap_rays, n, rgb, depth, acc);
+    k_write_render<<<(n + 255) / 256, 256, 0, s>>>(b.ray_out, b.cap_rays, n, rgb, depth, acc, b.offsets + n,
+                                                   render_sample_counter(b));
 }
 
 }  // namespace nm
