@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--only-large-map", action="store_true",
                    help="run only the large-map leg (reduced sizes for profiler captures) and print its JSON")
     p.add_argument("--ablation", action="store_true", help="also run the Sigma_D-weighting ablation (about 1 min)")
+    p.add_argument("--quality-full", action="store_true",
+                   help="run only the full-size training-quality comparison (about 10 min) and print its JSON")
     p.add_argument("--serving-seconds", type=float, default=6.0)
     p.add_argument("--rays", type=int, default=N_RAYS)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -209,43 +211,54 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- quality
 
-def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, H=120, seed=0,
-                sigma_floor=0.2, ray_seed=0, outlier_frac=0.0, depth_weighting="sigma_d"):
-    """Fits the room from noisy 320x240 keyframes (depth noise sigma_d >= sigma_floor
-    metres) along a smooth seeded camera path
-    (a Catmull-Rom spline through 8 interior points) for `steps` mapping steps and
-    returns PSNR (dB) and depth-L1 (m, along the ray) of held-out views of the same
-    path (every `every`-th pose, offset by half a period, never trained on) against
-    the analytic ground truth, before and after training.
-
-    outlier_frac: fraction of keyframe pixels with a gross depth error reported with
-    sigma_d = 1 m.  depth_weighting: "sigma_d" (the paper's loss, each pixel's depth
-    residual divided by its variance Sigma_D), "raw" (every pixel's variance replaced
-    by the median variance of the non-outlier pixels: the same overall depth weight,
-    no down-weighting of the outliers) or "none" (lambda_D = 0, colour only)."""
-    import numpy as np
+def quality_workload(n_poses=60, every=6, kf_W=320, kf_H=240, view_W=160, view_H=120, seed=0, sigma_floor=0.2,
+                     outlier_frac=0.0):
+    """Keyframes and held-out views for a training-quality fit of the procedural room:
+    `n_poses` poses on a smooth seeded camera path (a Catmull-Rom spline through 8
+    interior points); every `every`-th pose (offset by half a period) is held out and
+    rendered analytically at view_W x view_H without noise; the others become
+    kf_W x kf_H keyframes with depth noise sigma_d = max(0.01 z^2 U[0.5, 2],
+    sigma_floor) (and `outlier_frac` of gross depth errors reported with sigma_d = 1 m)."""
     import synth
-    from paper_2210_13641_gb300 import NerfMap, pack_params
-    cfg = synth.config_c2(precision=precision)
     room = synth.make_room(seed)
     poses = synth.room_spline_poses(room, n_poses, seed=seed + 5)
     held = set(range(every // 2, n_poses, every))
     train = [p for i, p in enumerate(poses) if i not in held]
-    kfs = synth.room_keyframes(room, len(train), seed=seed + 1, W=320, H=240, K=(262.5, 262.5, 160.0, 120.0),
-                               poses=train, sigma_floor=sigma_floor, outlier_frac=outlier_frac)
+    Kk = (525.0 * kf_W / 640, 525.0 * kf_H / 480, kf_W / 2.0, kf_H / 2.0)
+    kfs = synth.room_keyframes(room, len(train), seed=seed + 1, W=kf_W, H=kf_H, K=Kk, poses=train,
+                               sigma_floor=sigma_floor, outlier_frac=outlier_frac)
+    Kv = (525.0 * view_W / 640, 525.0 * view_H / 480, view_W / 2.0, view_H / 2.0)
+    views = synth.room_keyframes(room, len(held), seed=seed + 9, W=view_W, H=view_H, K=Kv, noise_k=0.0,
+                                 poses=[poses[i] for i in sorted(held)])
+    return {"room": room, "kfs": kfs, "views": views, "seed": seed, "view_wh": (view_W, view_H)}
+
+
+def quality_fit(wl, precision, steps, rays, ray_seed=0, depth_weighting="sigma_d"):
+    """Fits the map to the workload's keyframes for `steps` mapping steps of `rays`
+    rays and returns PSNR (dB) and depth-L1 (m, along the ray) of the held-out views
+    against the analytic ground truth, before and after training.
+
+    depth_weighting: "sigma_d" (the paper's loss, each pixel's depth residual divided
+    by its variance Sigma_D), "raw" (every pixel's variance replaced by the median
+    variance of the non-outlier pixels: the same overall depth weight, no
+    down-weighting of the outliers) or "none" (lambda_D = 0, colour only)."""
+    import numpy as np
+    import synth
+    from paper_2210_13641_gb300 import NerfMap, pack_params
+    seed = wl["seed"]
+    cfg = synth.config_c2(precision=precision)
+    kfs = wl["kfs"]
     if depth_weighting == "raw":
         good = np.concatenate([k.var[k.var < 1.0].ravel() for k in kfs])
         v0 = np.float32(np.median(good))
-        for k in kfs:
-            k.var = np.full_like(k.var, v0)
+        kfs = [synth.Keyframe(k.kf_id, k.c2w, k.K, k.W, k.H, k.rgb, k.depth, np.full_like(k.var, v0),
+                              depth_is_z=k.depth_is_z) for k in kfs]
     elif depth_weighting == "none":
         cfg = cfg.replace(lambda_d=np.float32(0.0))
     elif depth_weighting != "sigma_d":
         raise ValueError(depth_weighting)
-    bits = synth.room_occupancy_bits(room, cfg.occ_res, cfg.grid_origin, cfg.grid_inv_size)
-    Kv = (525.0 * W / 640, 525.0 * H / 480, W / 2.0, H / 2.0)
-    views = synth.room_keyframes(room, len(held), seed=seed + 9, W=W, H=H, K=Kv, noise_k=0.0,
-                                 poses=[poses[i] for i in sorted(held)])
+    bits = synth.room_occupancy_bits(wl["room"], cfg.occ_res, cfg.grid_origin, cfg.grid_inv_size)
+    W, H = wl["view_wh"]
     m = NerfMap(cfg, occ_every=0)
     m.set_params(pack_params(synth.random_params(cfg, seed)))
     m.set_occupancy(bits)
@@ -254,7 +267,7 @@ def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, 
 
     def evaluate():
         ps, dl = [], []
-        for v in views:
+        for v in wl["views"]:
             rgb, dep, _ = m.render(v.c2w, v.K, W, H)
             uu, vv = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
             s = np.sqrt(((uu - v.K[2]) / v.K[0]) ** 2 + ((vv - v.K[3]) / v.K[1]) ** 2 + 1.0)
@@ -264,6 +277,8 @@ def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, 
         return float(np.mean(ps)), float(np.mean(dl))
 
     p0, d0 = evaluate()
+    import torch
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(steps):
         m.step(rays, seed=ray_seed, want_loss=False)
@@ -272,9 +287,42 @@ def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, 
     p1, d1 = evaluate()
     m.close()
     return {"precision": precision, "steps": steps, "rays_per_step": rays, "train_keyframes": len(kfs),
-            "outlier_frac": outlier_frac, "depth_weighting": depth_weighting,
-            "heldout_views": len(views), "psnr_db": p1, "depth_l1_m": d1, "psnr_db_init": p0,
-            "depth_l1_m_init": d0, "final_loss": loss, "train_s": t}
+            "depth_weighting": depth_weighting, "heldout_views": len(wl["views"]), "psnr_db": p1,
+            "depth_l1_m": d1, "psnr_db_init": p0, "depth_l1_m_init": d0, "final_loss": loss, "train_s": t}
+
+
+def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, H=120, seed=0,
+                sigma_floor=0.2, ray_seed=0, outlier_frac=0.0, depth_weighting="sigma_d"):
+    """The reduced training-quality fit (50 keyframes of 320x240, 160x120 held-out
+    views): quality_workload + quality_fit."""
+    wl = quality_workload(n_poses=n_poses, every=every, view_W=W, view_H=H, seed=seed, sigma_floor=sigma_floor,
+                          outlier_frac=outlier_frac)
+    r = quality_fit(wl, precision, steps, rays, ray_seed=ray_seed, depth_weighting=depth_weighting)
+    r["outlier_frac"] = outlier_frac
+    return r
+
+
+def quality_full(precisions=("fp32", "fp16", "bf16"), seeds=(0, 1, 2), steps=2000, rays=1 << 18):
+    """The training configuration at its stated size: 100 keyframes of 640x480 along
+    the seeded spline (110 poses, every 11th held out: 10 held-out 640x480 views),
+    depth noise sigma_d = 0.01 z^2 U[0.5, 2] with no floor, `steps` steps of `rays`
+    rays (lr 1e-2, beta (0.9, 0.99)), each form fitted with every ray seed from the
+    same initial parameters; PSNR / depth-L1 per fit and per-form means."""
+    import statistics as st
+    t0 = time.perf_counter()
+    wl = quality_workload(n_poses=110, every=11, kf_W=640, kf_H=480, view_W=640, view_H=480, sigma_floor=0.0)
+    out = {"workload": "room, 100 keyframes 640x480 on a seeded spline, 10 held-out 640x480 views, "
+                       f"{steps} steps of {rays} rays", "generation_s": time.perf_counter() - t0, "fits": []}
+    for prec in precisions:
+        for sd in seeds:
+            out["fits"].append(quality_fit(wl, prec, steps, rays, ray_seed=sd))
+    for prec in precisions:
+        fs = [f for f in out["fits"] if f["precision"] == prec]
+        ps, dl = [f["psnr_db"] for f in fs], [f["depth_l1_m"] for f in fs]
+        out[prec] = {"psnr_db_mean": st.mean(ps), "psnr_db_sd": st.stdev(ps) if len(ps) > 1 else 0.0,
+                     "depth_l1_m_mean": st.mean(dl), "depth_l1_m_sd": st.stdev(dl) if len(dl) > 1 else 0.0,
+                     "train_s_mean": st.mean(f["train_s"] for f in fs)}
+    return out
 
 
 # ----------------------------------------------------------------- depth weighting
@@ -387,7 +435,7 @@ def large_map_benchmark(n_kf=2000, W=1200, H=680, rays=1 << 20, steps=5, warmup=
 
 # ----------------------------------------------------------------- serving
 
-def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0):
+def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0, group_renders=True):
     """Four resident scenes (tables 2^16 .. 2^19 per level, the room workload) with
     continuous mapping (2^16-ray steps), each receiving a 640x480 keyframe at 10 Hz,
     plus render queries (160x120, 640x480, 1280x720) arriving as a Poisson stream of
@@ -398,7 +446,7 @@ def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0):
     from paper_2210_13641_gb300 import pack_params
     from paper_2210_13641_gb300.binding import MapServer
     rng = np.random.default_rng(seed)
-    server = MapServer(max_scenes=4, max_inflight=2, step_rays=1 << 16)
+    server = MapServer(max_scenes=4, max_inflight=2, step_rays=1 << 16, group_renders=group_renders)
     scenes = []
     for j, log2t in enumerate((16, 17, 18, 19)):
         cfg = synth.config_c2(precision=precision, log2_table=log2t, seed=j)
@@ -452,9 +500,11 @@ def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0):
         if tag:
             lat.setdefault("render_" + tag, []).append(d["t_done"] - d["t_submit"])
     pct = lambda v, q: float(np.percentile(np.array(v) * 1e3, q))
-    out = {"precision": precision, "window_s": round(elapsed, 2),
+    out = {"precision": precision, "window_s": round(elapsed, 2), "group_renders": bool(group_renders),
            "mapping_rays_per_s": (st1["rays_done"] - st0["rays_done"]) / elapsed,
-           "requests": {k: len(v) for k, v in lat.items()}}
+           "requests": {k: len(v) for k, v in lat.items()},
+           "grouped_renders": st1["grouped_renders"] - st0["grouped_renders"],
+           "group_batches": st1["group_batches"] - st0["group_batches"]}
     for k, v in lat.items():
         out[f"{k}_ms_p50"] = pct(v, 50)
         out[f"{k}_ms_p99"] = pct(v, 99)
@@ -628,6 +678,14 @@ def main():
     if args.impl == "reference":
         os.environ.update(ONE_THREAD)                  # before numpy is first imported
         run_reference(args, rank, world)
+        return
+
+    if args.quality_full:
+        import torch
+        torch.cuda.set_device(local)
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps({"quality_full": quality_full(steps=args.steps if args.steps != 20 else 2000)}), flush=True)
         return
 
     if args.only_large_map:
@@ -804,6 +862,9 @@ def main():
     serving = None
     if not args.no_serving and rank == 0:
         serving = {p: serving_benchmark(p, kfs, bits, args.serving_seconds) for p in (args.precision, "fp32")}
+        if args.precision != "fp32":
+            serving[args.precision + "_ungrouped"] = serving_benchmark(args.precision, kfs, bits, args.serving_seconds,
+                                                                       group_renders=False)
     large = None
     if not args.no_large_map and rank == 0:
         large = large_map_benchmark(n_kf=args.large_map_keyframes, rays=args.large_map_rays,

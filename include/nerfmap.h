@@ -223,6 +223,28 @@ const float* map_loss_device(map_handle h);
 int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, uint32_t H,
                float* out_rgb, float* out_depth, float* out_acc, int mem_kind, void* stream);
 
+/*
+ * map_render_group - forward-only renders of n views of one or more maps in shared
+ * launches (the serving pattern: render queries of several resident scenes and of
+ * different resolutions batched together).  View i shows maps[i] (maps may repeat)
+ * from c2w[12 i .. 12 i + 11] with intrinsics K[4 i .. 4 i + 3] at W[i] x H[i]
+ * pixels; its colour goes to out_rgb[i] (device, H*W*3 floats) and its expected ray
+ * distance to out_depth[i] (device, H*W floats); out_rgb / out_depth or an entry may
+ * be NULL.  c2w, K, W, H, out_rgb and out_depth are host arrays of n entries.  The
+ * views are cut into batches of up to 2^18 rays; each batch runs as one sequence of
+ * launches (ray casting, march with each map's box and occupancy bitfield,
+ * compaction, a persistent tensor-core field forward over 128-sample tiles that
+ * never mix two views, switching weights where the map changes, compositing with
+ * each map's render_t_min, output).  Every pixel goes through the arithmetic of
+ * map_render of its view, and the images equal map_render's bit for bit.  Every map
+ * must use the FP16 or BF16 MLP (plain FP32 maps: map_render).  All work is queued
+ * on `stream`; the caller orders it after any work that changes the maps.  Work
+ * buffers are held by maps[0] (allocated on first use).  Errors: MAP_EINVAL
+ * (message on maps[0]), MAP_ENOMEM, MAP_ECUDA.
+ */
+int map_render_group(const map_handle* maps, uint32_t n, const float* c2w, const float* K, const uint32_t* W,
+                     const uint32_t* H, float* const* out_rgb, float* const* out_depth, void* stream);
+
 /* Parameter I/O.  Layout (FP32): tables [L][2^log2_table][F], then W1 [64][32],
  * W2 [16][64], W3 [64][32], W4 [64][64], W5 [3][64], each (out, in) row-major.
  * n must equal map_stats.param_count.  get/set wait for the stream. */
@@ -374,6 +396,18 @@ int map_march_noalloc(const map_config* cfg, const uint8_t* occ_bits, const floa
  * estimated footprint (tables, gradients, Adam moments, occupancy, step workspace,
  * kf_reserve_bytes of keyframes) plus hbm_reserve_bytes; otherwise the call returns
  * MAP_ENOMEM and may be retried once scenes have been removed or memory freed.
+ *
+ * Grouped renders (group_renders = 1): in each round of the worker, the render
+ * queries at the head of the queues of all scenes with a tensor-core MLP (per MLP
+ * type) are evaluated together, whatever their resolutions: the views are cut into
+ * batches of up to 2^18 rays, and each batch runs as one sequence of shared launches
+ * (ray casting, march with each scene's box and bitfield, compaction, a persistent
+ * tensor-core field forward whose 128-sample tiles never mix two views and which
+ * switches weights where the scene changes, compositing, output).  Every pixel goes
+ * through the arithmetic of a render of its view alone, so the results are the same
+ * bit for bit.  The grouped render runs on the server's own stream after the work
+ * each scene has already queued, and each scene's later work waits for it.  Plain
+ * FP32 scenes render on their own streams.
  */
 typedef struct map_server_s* map_server;
 
@@ -385,7 +419,8 @@ typedef struct map_server_config {
     uint32_t max_scenes;        /* scene slots, 1..64 */
     uint32_t max_inflight;      /* requests per scene on the GPU at once (>= 1) */
     uint32_t step_rays;         /* rays of a continuous-mapping step */
-    uint32_t reserved0;
+    uint32_t group_renders;     /* 1: render queries of the FP16 / BF16 scenes that are due together
+                                   run as one grouped render (see below); 0: each on its own */
     size_t hbm_reserve_bytes;   /* device memory left free at admission */
     size_t kf_reserve_bytes;    /* keyframe memory budgeted per scene */
     uint64_t seed;              /* reserved (each scene draws its rays from its map_config seed) */
@@ -414,6 +449,8 @@ typedef struct map_server_stats {
     uint64_t device_bytes;  /* admitted scenes' estimated footprints */
     uint32_t n_scenes;
     uint32_t pending;       /* requests submitted and not yet polled */
+    uint64_t grouped_renders; /* render queries evaluated in grouped renders */
+    uint64_t group_batches;   /* grouped renders issued (each one or more shared launch sequences) */
 } map_server_stats;
 
 int map_server_create(const map_server_config* cfg, map_server* out);

@@ -59,7 +59,7 @@ class MapStats(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_scenes", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
-                ("step_rays", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("step_rays", ctypes.c_uint32), ("group_renders", ctypes.c_uint32),
                 ("hbm_reserve_bytes", ctypes.c_size_t), ("kf_reserve_bytes", ctypes.c_size_t),
                 ("seed", ctypes.c_uint64)]
 
@@ -72,7 +72,8 @@ class Completion(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("t_now", ctypes.c_double), ("rays_done", ctypes.c_uint64), ("steps_done", ctypes.c_uint64),
-                ("device_bytes", ctypes.c_uint64), ("n_scenes", ctypes.c_uint32), ("pending", ctypes.c_uint32)]
+                ("device_bytes", ctypes.c_uint64), ("n_scenes", ctypes.c_uint32), ("pending", ctypes.c_uint32),
+                ("grouped_renders", ctypes.c_uint64), ("group_batches", ctypes.c_uint64)]
 
 
 REQ_KEYFRAME, REQ_STEP, REQ_RENDER = 0, 1, 2
@@ -94,6 +95,10 @@ _SIGS = {
     "map_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                                   ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p]),
+    "map_render_group": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.c_void_p]),
     "map_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     "map_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     "map_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
@@ -454,9 +459,9 @@ class MapServer:
     """Multi-scene serving loop (map_server_* of the C ABI)."""
 
     def __init__(self, max_scenes=4, max_inflight=2, step_rays=1 << 18, hbm_reserve=1 << 30,
-                 kf_reserve=1 << 30, seed=0):
+                 kf_reserve=1 << 30, seed=0, group_renders=True):
         self.lib = load()
-        c = ServerConfig(max_scenes, max_inflight, step_rays, 0, hbm_reserve, kf_reserve, seed)
+        c = ServerConfig(max_scenes, max_inflight, step_rays, int(group_renders), hbm_reserve, kf_reserve, seed)
         h = ctypes.c_void_p()
         rc = self.lib.map_server_create(ctypes.byref(c), ctypes.byref(h))
         if rc != MAP_OK:
@@ -565,6 +570,24 @@ class MapServer:
         st = ServerStats()
         self.lib.map_server_get_stats(self.h, ctypes.byref(st))
         return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+
+def render_group(maps, views, outs, stream=None):
+    """map_render_group: maps [n] NerfMap, views [n] of (c2w [3,4], K [4], W, H), outs
+    [n] of (rgb, depth) CUDA tensors ([H,W,3] and [H,W], either may be None)."""
+    n = len(maps)
+    lib = load()
+    hs = (ctypes.c_void_p * n)(*[m.h.value for m in maps])
+    c2w = np.ascontiguousarray(np.stack([np.asarray(v[0], np.float32).reshape(12) for v in views]))
+    K = np.ascontiguousarray(np.stack([np.asarray(v[1], np.float32).reshape(4) for v in views]))
+    W = np.array([v[2] for v in views], np.uint32)
+    H = np.array([v[3] for v in views], np.uint32)
+    rgb = (ctypes.c_void_p * n)(*[o[0].data_ptr() if o[0] is not None else None for o in outs])
+    dep = (ctypes.c_void_p * n)(*[o[1].data_ptr() if o[1] is not None else None for o in outs])
+    rc = lib.map_render_group(hs, n, c2w.ctypes.data, K.ctypes.data, W.ctypes.data, H.ctypes.data, rgb, dep,
+                              _stream(stream))
+    if rc != MAP_OK:
+        raise MapError(rc, lib.map_last_error(maps[0].h).decode())
 
 
 def marginal_covariances(C, P, blk, e, stream=None):

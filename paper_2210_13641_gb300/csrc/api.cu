@@ -74,6 +74,7 @@ struct map_scene {
     bool prof_on = false;
     std::vector<PhaseRec> prof;
     std::string err;
+    GroupBufs group{};              // work buffers of map_render_group calls led by this map
 };
 
 namespace {
@@ -277,6 +278,16 @@ void prof_clear(map_scene* h) {
 }  // namespace
 
 namespace nm {
+bool scene_view(const ::map_scene* h, SceneView* out) {
+    if (!h || !out) return false;
+    out->dc = h->dc;
+    out->dc.t_min = h->cfg.render_t_min;
+    out->params = h->params;
+    out->occ = h->occ_bits;
+    out->precision = h->cfg.precision;
+    return true;
+}
+
 void clear_global_error() { g_global_error.clear(); }
 void set_global_error(const char* msg) { g_global_error = msg; }
 }  // namespace nm
@@ -381,6 +392,7 @@ int map_destroy(map_handle h) {
     if (h->active_ev) cudaEventDestroy(h->active_ev);
     for (auto& a : h->allocs) cudaFree(a.first);
     h->allocs.clear();
+    if (h->group.items) group_bufs_free(h->group);
     delete h;
     return MAP_OK;
 }
@@ -739,6 +751,46 @@ int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, 
         NM_CUDA(h, cudaStreamSynchronize(s));  // the staging buffer is reused by the next chunk
     }
     return mem_kind == MAP_MEM_DEVICE ? MAP_OK : check_device_flags(h, s);
+}
+
+int map_render_group(const map_handle* maps, uint32_t n, const float* c2w, const float* K, const uint32_t* W,
+                     const uint32_t* H, float* const* out_rgb, float* const* out_depth, void* stream) {
+    if (!maps || n == 0 || !maps[0] || !c2w || !K || !W || !H) return MAP_EINVAL;
+    map_scene* lead = maps[0];
+    std::vector<GroupView> views[2];  // FP16, BF16
+    uint32_t stride = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        GroupView gv{};
+        if (!maps[i] || !scene_view(maps[i], &gv.scene)) return fail(lead, MAP_EINVAL, "null map in the group");
+        if (gv.scene.precision == MAP_PREC_FP32)
+            return fail(lead, MAP_EINVAL, "map_render_group: plain FP32 maps render with map_render");
+        if (W[i] == 0 || H[i] == 0 || (uint64_t)W[i] * H[i] > (1u << 24))
+            return fail(lead, MAP_EINVAL, "map_render_group: bad view size");
+        std::memcpy(gv.c2w, c2w + 12 * (size_t)i, sizeof(gv.c2w));
+        std::memcpy(gv.K, K + 4 * (size_t)i, sizeof(gv.K));
+        gv.W = W[i];
+        gv.H = H[i];
+        gv.out_rgb = out_rgb ? out_rgb[i] : nullptr;
+        gv.out_depth = out_depth ? out_depth[i] : nullptr;
+        stride = std::max(stride, gv.scene.dc.max_samples);
+        views[gv.scene.precision == MAP_PREC_BF16 ? 1 : 0].push_back(gv);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (lead->group.row_stride < stride) {
+        if (lead->group.items) {
+            cudaStreamSynchronize(s);
+            group_bufs_free(lead->group);
+        }
+        if (group_bufs_alloc(lead->group, kRenderChunk, std::max<uint32_t>(stride, 128)) != MAP_OK)
+            return fail(lead, MAP_ENOMEM, "map_render_group: work buffers");
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (views[k].empty()) continue;
+        const int rc = render_group(views[k].data(), (uint32_t)views[k].size(), k == 1, lead->group, lead->n_sm, s,
+                                    &lead->launches);
+        if (rc) return fail(lead, rc, "map_render_group: launch failed");
+    }
+    return MAP_OK;
 }
 
 int map_get_params(map_handle h, float* dst, size_t n, int mem_kind, void* stream) {

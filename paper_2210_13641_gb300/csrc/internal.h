@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 
+struct map_scene;  // the state behind a map_handle (api.cu)
+
 namespace nm {
 
 // Message slot of the calls that take no map handle (map_create,
@@ -60,6 +62,76 @@ inline unsigned long long* render_sample_counter(const StepBufs& b) {
     return reinterpret_cast<unsigned long long*>(b.loss + 8);
 }
 
+// ---------------------------------------------------------------- grouped render
+// One piece of a grouped render (several views of several scenes in shared
+// launches): pixels pix0 .. pix0 + n_rays - 1 of a W-wide view of one scene, which are
+// rays ray0 .. ray0 + n_rays - 1 of the batch.  s0, n_s, tile0, n_tiles are written on
+// the device after the march's scan: the piece's samples s0 .. s0 + n_s - 1 and its
+// 128-sample tiles tile0 .. tile0 + n_tiles - 1 of the batch.
+struct GroupItem {
+    DevCfg c;                 // the scene's configuration (t_min: its render threshold)
+    const float* params;      // the scene's parameters (tables, then MLP weights)
+    const uint32_t* occ;      // its occupancy bitfield (nullptr: none)
+    float c2w[12];
+    float K[4];
+    uint32_t W;
+    uint32_t pix0, ray0, n_rays;
+    float* out_rgb;           // the view's device outputs: [pixels][3] colour, [pixels] depth
+    float* out_depth;
+    uint32_t s0, n_s, tile0, n_tiles;
+};
+constexpr int kGroupMaxItems = 8;
+struct GroupItems {
+    GroupItem it[kGroupMaxItems];
+};
+
+// Work buffers of grouped renders: a ray batch of cap_rays rays with row_stride slots
+// per ray (the largest max_samples of the scenes it serves), the piece table and the
+// batch's tile count.
+struct GroupBufs {
+    StepBufs b{};
+    uint32_t row_stride = 0;
+    GroupItem* items = nullptr;     // [kGroupMaxItems], device
+    uint32_t* n_tiles = nullptr;    // [1], device
+};
+
+// A scene's state as a grouped render needs it (api.cu).
+struct SceneView {
+    DevCfg dc;                      // t_min set to the scene's render threshold
+    const float* params;
+    const uint32_t* occ;
+    uint32_t precision;             // MAP_PREC_*
+};
+bool scene_view(const ::map_scene* h, SceneView* out);
+
+// One view of a grouped render: the scene, the camera and the device outputs.
+struct GroupView {
+    SceneView scene;
+    float c2w[12];
+    float K[4];
+    uint32_t W, H;
+    float* out_rgb;                 // device, [H*W][3]
+    float* out_depth;               // device, [H*W]
+};
+
+// k_group.cu: allocation of the work buffers, and the grouped render of `n` views whose
+// scenes all use the FP16 (bf16 = false) or all the BF16 tensor-core MLP, in chunks of
+// at most cap_rays rays / kGroupMaxItems pieces; every launch is queued on s.
+int group_bufs_alloc(GroupBufs& g, uint32_t cap_rays, uint32_t row_stride);
+void group_bufs_free(GroupBufs& g);
+// launches (nullable) is increased by the number of kernels launched.
+int render_group(const GroupView* views, uint32_t n, bool bf16, GroupBufs& g, int n_sm, cudaStream_t s,
+                 uint64_t* launches);
+
+// k_field_tc.cu: the grouped forward (persistent; switches weights where the scene
+// changes between tiles).
+void launch_group_fwd_tc(const GroupItem* items, uint32_t n_items, const uint32_t* n_tiles, const StepBufs& b,
+                         bool bf16, int n_sm, cudaStream_t s);
+// k_composite.cu: the grouped render's compositing (each ray's spacing and
+// termination threshold from its piece) and output write.
+void launch_composite_group(const GroupItem* items, uint32_t n_rays, const StepBufs& b, cudaStream_t s);
+void launch_write_group(const GroupItem* items, uint32_t n_rays, const StepBufs& b, cudaStream_t s);
+
 // k_rays.cu
 void launch_set_kf_desc(KfDesc* table, uint32_t idx, const KfDesc& d, cudaStream_t s);
 void launch_keyframe_texels(const float* rgb, const float* depth, const float* var, uint32_t W,
@@ -73,6 +145,11 @@ void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, co
                   cudaStream_t s);
 
 // tile_sums: at least ceil(n / kScanTile) words.
+// k_compact: each ray's retained steps from its slot row (row_stride floats per ray)
+// to its scanned offset, with the ray index beside each sample.
+void launch_compact(uint32_t n_rays, uint32_t row_stride, const uint32_t* offsets, const float* slots,
+                    uint32_t* ray_id, float* ts, cudaStream_t s);
+
 void launch_scan_counts(const uint32_t* counts, uint32_t n, uint32_t* offsets, uint32_t* tile_sums,
                         cudaStream_t s);
 

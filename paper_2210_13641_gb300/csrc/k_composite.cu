@@ -59,18 +59,27 @@ __device__ __forceinline__ float warp_suffix(float x, uint32_t lane) {
 // its gradient scales.  In the forward-only form (render) a ray stops at the first
 // sample whose transmittance is below t_min.  scratch holds (w_i, T_{i+1}) between
 // the two passes and then (dL/dsigma_i, dL/dc_i).
-template <bool kBackward>
+// kGroup (render only): the rays of a grouped render, each taking its sample spacing
+// and termination threshold from its piece (items[ray's kKf plane]).
+template <bool kBackward, bool kGroup = false>
 __global__ void __launch_bounds__(kCompositeWarps * 32) k_composite(
     DevCfg c, uint32_t n_rays, const float* __restrict__ rays, uint32_t cap, const uint32_t* __restrict__ offsets,
     const float* __restrict__ ts, const float4* __restrict__ sig_rgb, float4* __restrict__ scratch,
-    float* __restrict__ ray_out, float* __restrict__ loss, float* __restrict__ partials) {
+    float* __restrict__ ray_out, float* __restrict__ loss, float* __restrict__ partials,
+    const GroupItem* __restrict__ items = nullptr) {
+    static_assert(!(kBackward && kGroup), "grouped compositing is forward only");
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const uint32_t n_warps = gridDim.x * kCompositeWarps;
-    const float delta = c.step_t;
+    float delta = c.step_t, t_min = c.t_min;
     float l = 0.f;     // this warp's loss sum (lane 0)
     float gmax = 0.f;  // largest per-sample density seed |dL/dsigma * sigma|
     float cmax = 0.f;  // largest per-sample colour seed |dL/dc|
     for (uint32_t r = blockIdx.x * kCompositeWarps + wib; r < n_rays; r += n_warps) {
+        if (kGroup) {
+            const GroupItem& it = items[__float_as_uint(rays[kKf * cap + r])];
+            delta = it.c.step_t;
+            t_min = it.c.t_min;
+        }
         const uint32_t a = offsets[r], b = offsets[r + 1];
         float carry = 0.f;  // sum of sigma delta over the earlier chunks
         float Ir = 0.f, Ig = 0.f, Ib = 0.f, Dh = 0.f, acc = 0.f;
@@ -85,7 +94,7 @@ __global__ void __launch_bounds__(kCompositeWarps * 32) k_composite(
             if (lane == 0) excl = 0.f;
             const float T = expf(-(carry + excl));
             bool live = in;
-            if (!kBackward) live = live && !(T < c.t_min);
+            if (!kBackward) live = live && !(T < t_min);
             const float w = live ? T * -expm1f(-tau) : 0.f;
             Ir += w * v.y;
             Ig += w * v.z;
@@ -94,7 +103,7 @@ __global__ void __launch_bounds__(kCompositeWarps * 32) k_composite(
             acc += w;
             if (kBackward && in) scratch[s] = make_float4(w, expf(-(carry + incl)), 0.f, 0.f);
             carry += __shfl_sync(kFull, incl, 31);
-            if (!kBackward && __any_sync(kFull, in && T < c.t_min)) break;
+            if (!kBackward && __any_sync(kFull, in && T < t_min)) break;
         }
         Ir = warp_sum(Ir);
         Ig = warp_sum(Ig);
@@ -200,8 +209,7 @@ __global__ void __launch_bounds__(kCompositeWarps * 32) k_composite(
     }
 }
 
-void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const StepBufs& b,
-                      cudaStream_t s) {
+static uint32_t composite_grid(uint32_t n_rays) {
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -211,6 +219,18 @@ void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const Ste
     if (cap > kCompositeMaxBlocks) cap = kCompositeMaxBlocks;
     if (grid > cap) grid = cap;
     if (grid == 0) grid = 1;
+    return grid;
+}
+
+void launch_composite_group(const GroupItem* items, uint32_t n_rays, const StepBufs& b, cudaStream_t s) {
+    DevCfg unused{};
+    k_composite<false, true><<<composite_grid(n_rays), kCompositeWarps * 32, 0, s>>>(
+        unused, n_rays, b.rays, b.cap_rays, b.offsets, b.t, b.sig_rgb, nullptr, b.ray_out, nullptr, nullptr, items);
+}
+
+void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const StepBufs& b,
+                      cudaStream_t s) {
+    const uint32_t grid = composite_grid(n_rays);
     if (backward) {
         cudaMemsetAsync(b.loss, 0, 4 * sizeof(float), s);
         k_composite<true><<<grid, kCompositeWarps * 32, 0, s>>>(c, n_rays, b.rays, b.cap_rays, b.offsets, b.t,
@@ -243,6 +263,25 @@ __global__ void k_write_render(const float* __restrict__ ray_out, uint32_t cap, 
     }
     if (depth) depth[r] = ray_out[3 * cap + r];
     if (acc) acc[r] = ray_out[4 * cap + r];
+}
+
+// Grouped render output: ray r of piece j is pixel pix0 + (r - ray0) of that piece's view.
+__global__ void k_write_group(const GroupItem* __restrict__ items, const float* __restrict__ rays,
+                              const float* __restrict__ ray_out, uint32_t cap, uint32_t n) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const GroupItem& it = items[__float_as_uint(rays[kKf * cap + r])];
+    const size_t p = it.pix0 + (r - it.ray0);
+    if (it.out_rgb) {
+        it.out_rgb[3 * p] = ray_out[r];
+        it.out_rgb[3 * p + 1] = ray_out[cap + r];
+        it.out_rgb[3 * p + 2] = ray_out[2 * cap + r];
+    }
+    if (it.out_depth) it.out_depth[p] = ray_out[3 * cap + r];
+}
+
+void launch_write_group(const GroupItem* items, uint32_t n_rays, const StepBufs& b, cudaStream_t s) {
+    k_write_group<<<(n_rays + 255) / 256, 256, 0, s>>>(items, b.rays, b.ray_out, b.cap_rays, n_rays);
 }
 
 void launch_write_render(const StepBufs& b, uint32_t n, float* rgb, float* depth, float* acc,

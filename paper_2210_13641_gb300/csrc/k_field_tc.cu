@@ -195,6 +195,143 @@ constexpr int kT32 = 128 * 32 * 2, kT64 = 128 * 64 * 2, kT16 = 128 * 16 * 2;
 constexpr int kFwdSmem = kWB + kT32 + kT64;                            // 45056
 
 // ------------------------------------------------------------------ forward
+// One tile of the forward: samples i0 .. i0 + count - 1 (count <= 128); thread r of
+// the block owns sample row r.  smem: the weight tiles, then tA (128 x 32: X0, X3) and
+// tB (128 x 64: H1, H3, H4; a layer's MMAs have completed before its output
+// overwrites its input).  Returns after the tile's last MMA wait.
+template <bool BF16>
+__device__ __forceinline__ void fwd_tile(const DevCfg& c, const float2* __restrict__ tables,
+                                         const float* __restrict__ rays, uint32_t cap,
+                                         const uint32_t* __restrict__ ray_id, const float* __restrict__ ts,
+                                         float4* __restrict__ sig_rgb, uint4* __restrict__ feat_out,
+                                         float feat_scale, uint32_t i0, uint32_t count, uint8_t* smem,
+                                         uint32_t tmem, uint64_t* bar, uint32_t& phase, bool& timed_out) {
+    uint8_t* sW1 = smem;
+    uint8_t* sW2 = sW1 + kW1B;
+    uint8_t* sW3 = sW2 + kW2B;
+    uint8_t* sW4 = sW3 + kW3B;
+    uint8_t* sW5 = sW4 + kW4B;
+    uint8_t* tA = smem + kWB;
+    uint8_t* tB = tA + kT32;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const float inv_fs = 1.f / feat_scale;
+    const uint32_t i = i0 + tid;
+    const bool valid = (uint32_t)tid < count;
+    float v[32];
+    float3 d = make_float3(0.f, 0.f, 0.f);
+    float3 x = make_float3(0.f, 0.f, 0.f);
+    if (valid) x = sample_pos_tc(c, rays, cap, ray_id[i], ts[i], d);
+    // one group of kGatherGroup = 4 levels = 8 features = one 16-byte chunk of the row
+#pragma unroll 1
+    for (int g = 0; g < kEnc / 8; ++g) {
+        if (valid) {
+            encode_group(c, tables, x, kGatherGroup * g, v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] *= feat_scale;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = 0.f;
+        }
+        uint4 q;
+        q.x = pack2<BF16>(v[0], v[1]);
+        q.y = pack2<BF16>(v[2], v[3]);
+        q.z = pack2<BF16>(v[4], v[5]);
+        q.w = pack2<BF16>(v[6], v[7]);
+        *reinterpret_cast<uint4*>(tA + tile_offset(tid, 8 * g, 128)) = q;
+        if (feat_out && valid) feat_out[(size_t)i * 4 + g] = q;
+    }
+    // layer 1: D = X0 W1^T (128 x 64)
+    to_tensor();
+    if (tid == 0) {
+        gemm(tmem, kmaj(tA, 128), kmaj(sW1, 64), 2, idesc_f16(128, 64, BF16, false, false), false);
+        mma_commit(bar);
+    }
+    wait_mma(bar, phase, timed_out, c.wait_polls);
+#pragma unroll
+    for (int h = 0; h < 64; h += 32) {  // 32-column halves keep fewer values live
+        ld_cols<32>(trow, h, v);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] *= inv_fs;
+        store_row_at<BF16, 32, true>(tB, tid, h, v);
+    }
+    // layer 2: y = H1 W2^T (128 x 16)
+    to_tensor();
+    if (tid == 0) {
+        gemm(tmem, kmaj(tB, 128), kmaj(sW2, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
+        mma_commit(bar);
+    }
+    wait_mma(bar, phase, timed_out, c.wait_polls);
+    ld_cols<16>(trow, 0, v);
+    const float sigma = expf(fminf(v[0], kSigmaHMax));
+    if (valid) sh16(d.x, d.y, d.z, v + kGeo);
+    else {
+#pragma unroll
+        for (int k = kGeo; k < 32; ++k) v[k] = 0.f;
+    }
+    store_row<BF16, 32>(tA, tid, v);
+    // layer 3: H3 = relu(X3 W3^T)
+    to_tensor();
+    if (tid == 0) {
+        gemm(tmem, kmaj(tA, 128), kmaj(sW3, 64), 2, idesc_f16(128, 64, BF16, false, false), false);
+        mma_commit(bar);
+    }
+    wait_mma(bar, phase, timed_out, c.wait_polls);
+#pragma unroll
+    for (int h = 0; h < 64; h += 32) {
+        ld_cols<32>(trow, h, v);
+        store_row_at<BF16, 32, true>(tB, tid, h, v);
+    }
+    // layer 4: H4 = relu(H3 W4^T)
+    to_tensor();
+    if (tid == 0) {
+        gemm(tmem, kmaj(tB, 128), kmaj(sW4, 64), 4, idesc_f16(128, 64, BF16, false, false), false);
+        mma_commit(bar);
+    }
+    wait_mma(bar, phase, timed_out, c.wait_polls);
+#pragma unroll
+    for (int h = 0; h < 64; h += 32) {
+        ld_cols<32>(trow, h, v);
+        store_row_at<BF16, 32, true>(tB, tid, h, v);
+    }
+    // layer 5: z = H4 W5^T (3 of 16 columns used)
+    to_tensor();
+    if (tid == 0) {
+        gemm(tmem, kmaj(tB, 128), kmaj(sW5, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
+        mma_commit(bar);
+    }
+    wait_mma(bar, phase, timed_out, c.wait_polls);
+    ld_cols<16>(trow, 0, v);
+    if (valid) sig_rgb[i] = make_float4(sigma, sigmoidf_(v[0]), sigmoidf_(v[1]), sigmoidf_(v[2]));
+}
+
+// Tensor memory and barriers of a forward block: 64 TMEM columns (one 128 x 64 FP32
+// accumulator), the MMA barrier and the drain barrier.
+__device__ __forceinline__ uint32_t fwd_block_setup(uint32_t* tslot, uint64_t* bar, uint64_t* drain_bar) {
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(tslot, 64);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(drain_bar, 1);
+        mbar_fence_init();
+    }
+    to_tensor();
+    return *tslot;
+}
+
+// End of a forward block: after a timeout, drain the issued MMAs; free the TMEM.
+__device__ __forceinline__ void fwd_block_finish(uint32_t tmem, uint64_t* drain_bar, bool timed_out) {
+    fence_before_sync();
+    const bool any_timeout = __syncthreads_or(timed_out) != 0;
+    fence_after_sync();
+    if (any_timeout) {
+        if (threadIdx.x == 0) drain_mma(drain_bar);
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+    }
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, 64);
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* __restrict__ params,
                                                       const float* __restrict__ rays, uint32_t cap,
@@ -206,137 +343,81 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar, drain_bar;
     __shared__ uint32_t tslot;
-    uint8_t* sW1 = smem;
-    uint8_t* sW2 = sW1 + kW1B;
-    uint8_t* sW3 = sW2 + kW2B;
-    uint8_t* sW4 = sW3 + kW3B;
-    uint8_t* sW5 = sW4 + kW4B;
-    uint8_t* tA = smem + kWB;   // X0, X3   (128 x 32)
-    uint8_t* tB = tA + kT32;    // H1, H3, H4 (128 x 64): a layer's MMAs have completed
-                                // before its output overwrites its input
-
-    const int tid = threadIdx.x, warp = tid >> 5;
-    load_weight_tiles<BF16>(params + (size_t)c.L * c.T * 2, sW1, sW2, sW3, sW4, sW5);
-    if (warp == 0) tmem_alloc(&tslot, 64);
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        mbar_init(&drain_bar, 1);
-        mbar_fence_init();
-    }
-    to_tensor();
-    const uint32_t tmem = tslot;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    load_weight_tiles<BF16>(params + (size_t)c.L * c.T * 2, smem, smem + kW1B, smem + kW1B + kW2B,
+                            smem + kW1B + kW2B + kW3B, smem + kW1B + kW2B + kW3B + kW4B);
+    const uint32_t tmem = fwd_block_setup(&tslot, &bar, &drain_bar);
     const uint32_t n = *n_total;
     const uint32_t n_tiles = (n + 127) / 128;
     const float2* tables = reinterpret_cast<const float2*>(params);
-    const float inv_fs = 1.f / feat_scale;
     uint32_t phase = 0;
     bool timed_out = false;
-
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint32_t i = tile * 128 + tid;
-        const bool valid = i < n;
-        float v[32];
-        float3 d = make_float3(0.f, 0.f, 0.f);
-        float3 x = make_float3(0.f, 0.f, 0.f);
-        if (valid) x = sample_pos_tc(c, rays, cap, ray_id[i], ts[i], d);
-        // one group of kGatherGroup = 4 levels = 8 features = one 16-byte chunk of the row
-#pragma unroll 1
-        for (int g = 0; g < kEnc / 8; ++g) {
-            if (valid) {
-                encode_group(c, tables, x, kGatherGroup * g, v);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] *= feat_scale;
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = 0.f;
-            }
-            uint4 q;
-            q.x = pack2<BF16>(v[0], v[1]);
-            q.y = pack2<BF16>(v[2], v[3]);
-            q.z = pack2<BF16>(v[4], v[5]);
-            q.w = pack2<BF16>(v[6], v[7]);
-            *reinterpret_cast<uint4*>(tA + tile_offset(tid, 8 * g, 128)) = q;
-            if (feat_out && valid) feat_out[(size_t)i * 4 + g] = q;
-        }
-        // layer 1: D = X0 W1^T (128 x 64)
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tA, 128), kmaj(sW1, 64), 2, idesc_f16(128, 64, BF16, false, false), false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out, c.wait_polls);
-#pragma unroll
-        for (int h = 0; h < 64; h += 32) {  // 32-column halves keep fewer values live
-            ld_cols<32>(trow, h, v);
-#pragma unroll
-            for (int k = 0; k < 32; ++k) v[k] *= inv_fs;
-            store_row_at<BF16, 32, true>(tB, tid, h, v);
-        }
-        // layer 2: y = H1 W2^T (128 x 16)
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tB, 128), kmaj(sW2, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out, c.wait_polls);
-        ld_cols<16>(trow, 0, v);
-        const float sigma = expf(fminf(v[0], kSigmaHMax));
-        if (valid) sh16(d.x, d.y, d.z, v + kGeo);
-        else {
-#pragma unroll
-            for (int k = kGeo; k < 32; ++k) v[k] = 0.f;
-        }
-        store_row<BF16, 32>(tA, tid, v);
-        // layer 3: H3 = relu(X3 W3^T)
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tA, 128), kmaj(sW3, 64), 2, idesc_f16(128, 64, BF16, false, false), false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out, c.wait_polls);
-#pragma unroll
-        for (int h = 0; h < 64; h += 32) {
-            ld_cols<32>(trow, h, v);
-            store_row_at<BF16, 32, true>(tB, tid, h, v);
-        }
-        // layer 4: H4 = relu(H3 W4^T)
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tB, 128), kmaj(sW4, 64), 4, idesc_f16(128, 64, BF16, false, false), false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out, c.wait_polls);
-#pragma unroll
-        for (int h = 0; h < 64; h += 32) {
-            ld_cols<32>(trow, h, v);
-            store_row_at<BF16, 32, true>(tB, tid, h, v);
-        }
-        // layer 5: z = H4 W5^T (3 of 16 columns used)
-        to_tensor();
-        if (tid == 0) {
-            gemm(tmem, kmaj(tB, 128), kmaj(sW5, 16), 4, idesc_f16(128, 16, BF16, false, false), false);
-            mma_commit(&bar);
-        }
-        wait_mma(&bar, phase, timed_out, c.wait_polls);
-        ld_cols<16>(trow, 0, v);
-        if (valid) sig_rgb[i] = make_float4(sigma, sigmoidf_(v[0]), sigmoidf_(v[1]), sigmoidf_(v[2]));
+        const uint32_t i0 = tile * 128;
+        fwd_tile<BF16>(c, tables, rays, cap, ray_id, ts, sig_rgb, feat_out, feat_scale, i0, min(128u, n - i0), smem,
+                       tmem, &bar, phase, timed_out);
         fence_before_sync();
         if (__syncthreads_or(timed_out)) {
-            if (tid == 0) atomicOr(err, kErrTimeout);
+            if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
             break;
         }
     }
-    fence_before_sync();
-    const bool any_timeout = __syncthreads_or(timed_out) != 0;
-    fence_after_sync();
-    if (any_timeout) {
-        if (tid == 0) drain_mma(&drain_bar);
+    fwd_block_finish(tmem, &drain_bar, timed_out);
+}
+
+// Grouped forward (render of several views of several scenes): the batch's tiles
+// are those of its pieces in order (a tile never mixes two pieces); a persistent
+// block takes tiles i, i + grid, ...; where a tile belongs to another piece than the
+// block's previous one, the block copies that piece's configuration into shared
+// memory and, if the scene differs, rounds that scene's weights into the operand
+// tiles.  Each tile is then exactly the single-view forward's tile.
+template <bool BF16>
+__global__ void __launch_bounds__(128, 4) k_group_fwd_tc(const GroupItem* __restrict__ items, uint32_t n_items,
+                                                      const uint32_t* __restrict__ n_tiles_total,
+                                                      const float* __restrict__ rays, uint32_t cap,
+                                                      const uint32_t* __restrict__ ray_id,
+                                                      const float* __restrict__ ts, float4* __restrict__ sig_rgb,
+                                                      float feat_scale, uint32_t* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar, drain_bar;
+    __shared__ uint32_t tslot;
+    __shared__ DevCfg cfg_s;
+    __shared__ uint32_t tile0_s[kGroupMaxItems + 1];
+    const uint32_t tmem = fwd_block_setup(&tslot, &bar, &drain_bar);
+    const uint32_t total = *n_tiles_total;
+    if (threadIdx.x < n_items) tile0_s[threadIdx.x] = items[threadIdx.x].tile0;
+    if (threadIdx.x == 0) tile0_s[n_items] = total;
+    __syncthreads();
+    const float* cur_params = nullptr;
+    uint32_t cur = n_items;  // no piece yet
+    uint32_t phase = 0;
+    bool timed_out = false;
+    for (uint32_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        uint32_t j = 0;
+        while (j + 1 < n_items && tile0_s[j + 1] <= tile) ++j;
+        const GroupItem& it = items[j];
+        if (j != cur) {
+            __syncthreads();  // every thread is done with the previous tile's configuration
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&it.c);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&cfg_s);
+            for (uint32_t w = threadIdx.x; w < sizeof(DevCfg) / 4; w += blockDim.x) dst[w] = src[w];
+            if (it.params != cur_params)
+                load_weight_tiles<BF16>(it.params + (size_t)it.c.L * it.c.T * 2, smem, smem + kW1B,
+                                        smem + kW1B + kW2B, smem + kW1B + kW2B + kW3B,
+                                        smem + kW1B + kW2B + kW3B + kW4B);
+            cur_params = it.params;
+            cur = j;
+            to_tensor();      // the weights to the tensor core, the configuration to every thread
+        }
+        const uint32_t k = (tile - tile0_s[j]) * 128;
+        fwd_tile<BF16>(cfg_s, reinterpret_cast<const float2*>(it.params), rays, cap, ray_id, ts, sig_rgb, nullptr,
+                       feat_scale, it.s0 + k, min(128u, it.n_s - k), smem, tmem, &bar, phase, timed_out);
         fence_before_sync();
-        __syncthreads();
-        fence_after_sync();
+        if (__syncthreads_or(timed_out)) {
+            if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+            break;
+        }
     }
-    if (warp == 0) tmem_dealloc(tmem, 64);
+    fwd_block_finish(tmem, &drain_bar, timed_out);
 }
 
 // ------------------------------------------------------------------ backward
@@ -727,6 +808,20 @@ void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, 
                          bool bf16, int n_sm, cudaStream_t s) {
     if (bf16) fwd_tc<true>(c, params, n_rays, b, store_feat, n_sm, s);
     else fwd_tc<false>(c, params, n_rays, b, store_feat, n_sm, s);
+}
+
+void launch_group_fwd_tc(const GroupItem* items, uint32_t n_items, const uint32_t* n_tiles, const StepBufs& b,
+                         bool bf16, int n_sm, cudaStream_t s) {
+    const float fs = bf16 ? 1.f : 256.f;
+    if (bf16) {
+        cudaFuncSetAttribute(k_group_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+        k_group_fwd_tc<true><<<n_sm * 4, 128, kFwdSmem, s>>>(items, n_items, n_tiles, b.rays, b.cap_rays, b.ray_id,
+                                                              b.t, b.sig_rgb, fs, b.err);
+    } else {
+        cudaFuncSetAttribute(k_group_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+        k_group_fwd_tc<false><<<n_sm * 4, 128, kFwdSmem, s>>>(items, n_items, n_tiles, b.rays, b.cap_rays,
+                                                               b.ray_id, b.t, b.sig_rgb, fs, b.err);
+    }
 }
 
 void launch_field_bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t n_rays, const StepBufs& b,

@@ -2,6 +2,7 @@
 // exclusive scan that compacts the retained samples (steps a1-a2 of the mapping
 // step; sampling follows Sec. 3.2 of the paper, the ray draw Sec. 3.3).
 #include "internal.h"
+#include "rays.cuh"
 
 namespace nm {
 
@@ -41,37 +42,6 @@ void launch_keyframe_texels(const float* rgb, const float* depth, const float* v
     const uint32_t n = W * H;
     k_keyframe_texels<<<(n + 255) / 256, 256, 0, s>>>(rgb, depth, var, W, H, K[0], K[1], K[2],
                                                        K[3], depth_is_z, texels);
-}
-
-// ---------------------------------------------------------------- ray casting
-// Back-projection of the pixel centre, rotation to world, normalisation; exact
-// FP32 operation order (the same integer decisions follow from these values).
-__device__ __forceinline__ void cast_ray(const float* c2w, const float* K, uint32_t u,
-                                         uint32_t v, float3& o, float3& d) {
-    const float dx = fdiv(fsub(fadd((float)u, 0.5f), K[2]), K[0]);
-    const float dy = fdiv(fsub(fadd((float)v, 0.5f), K[3]), K[1]);
-    const float wx = fadd(fadd(fmul(c2w[0], dx), fmul(c2w[1], dy)), c2w[2]);
-    const float wy = fadd(fadd(fmul(c2w[4], dx), fmul(c2w[5], dy)), c2w[6]);
-    const float wz = fadd(fadd(fmul(c2w[8], dx), fmul(c2w[9], dy)), c2w[10]);
-    const float n = __fsqrt_rn(fadd(fadd(fmul(wx, wx), fmul(wy, wy)), fmul(wz, wz)));
-    d = make_float3(fdiv(wx, n), fdiv(wy, n), fdiv(wz, n));
-    o = make_float3(c2w[3], c2w[7], c2w[11]);
-}
-
-__device__ __forceinline__ void store_ray(float* rays, uint32_t cap, uint32_t r, float3 o,
-                                          float3 d, float4 t0, float V, uint32_t kf) {
-    rays[kOx * cap + r] = o.x;
-    rays[kOy * cap + r] = o.y;
-    rays[kOz * cap + r] = o.z;
-    rays[kDx * cap + r] = d.x;
-    rays[kDy * cap + r] = d.y;
-    rays[kDz * cap + r] = d.z;
-    rays[kIr * cap + r] = t0.x;
-    rays[kIg * cap + r] = t0.y;
-    rays[kIb * cap + r] = t0.z;
-    rays[kD * cap + r] = t0.w;
-    rays[kV * cap + r] = V;
-    rays[kKf * cap + r] = __uint_as_float(kf);
 }
 
 // Uniform draw with replacement over (keyframe, pixel): keyframe = r0 mod n_kf,
@@ -253,6 +223,11 @@ __global__ void k_scan_add(uint32_t* __restrict__ out, uint32_t n,
                            const uint32_t* __restrict__ tile_sums) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] += tile_sums[i / kScanTile];
+}
+
+void launch_compact(uint32_t n_rays, uint32_t row_stride, const uint32_t* offsets, const float* slots,
+                    uint32_t* ray_id, float* ts, cudaStream_t s) {
+    k_compact<<<(n_rays + 7) / 8, 256, 0, s>>>(n_rays, row_stride, offsets, slots, ray_id, ts);
 }
 
 void launch_march(const DevCfg& c, const uint32_t* occ_bits, uint32_t n_rays, const StepBufs& b,

@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/nerfmap.h"
+#include "internal.h"
 
 namespace {
 
@@ -57,6 +58,7 @@ struct Request {
     float* out_rgb = nullptr;
     float* out_depth = nullptr;
     float loss = 0.f;
+    bool grouped = false;      // render issued in a grouped launch with other scenes' renders
 };
 
 struct Scene {
@@ -65,6 +67,7 @@ struct Scene {
     cudaStream_t stream = nullptr;
     bool mapping = false;
     bool has_keyframe = false;
+    uint32_t precision = 0;           // MAP_PREC_* of the scene's MLP
     uint32_t step_rays = 0;
     uint64_t seed = 0;
     uint64_t steps_issued = 0, steps_done = 0;
@@ -93,6 +96,13 @@ struct map_server_s {
     std::atomic<bool> stop{false};
     std::thread worker;
     std::atomic<uint64_t> rays_done{0};
+    // grouped renders (cfg.group_renders): their stream, work buffers and output arena
+    cudaStream_t group_stream = nullptr;
+    nm::GroupBufs gbufs{};
+    float* arena = nullptr;
+    size_t arena_floats = 0;
+    int n_sm = 0;
+    std::atomic<uint64_t> grouped_renders{0}, group_batches{0};
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 
@@ -201,11 +211,129 @@ bool issue_one(map_server_s* s, Scene& sc, Request* r) {
     return true;
 }
 
+constexpr uint32_t kGroupCapRays = 1u << 18;
+constexpr size_t kGroupMaxPixels = (size_t)1 << 22;  // pixels of one grouped batch
+
+// Renders at the head of the tensor-core scenes' queues, issued together: one grouped
+// render (shared launches over all their views) per MLP type on the group stream,
+// which first waits for the work each scene has already queued; each scene's later
+// work waits for the grouped render (it reads the scene's parameters).  Returns
+// whether anything was issued.
+bool issue_group(map_server_s* s) {
+    bool any = false;
+    for (uint32_t prec : {(uint32_t)MAP_PREC_FP16, (uint32_t)MAP_PREC_BF16}) {
+        std::vector<std::pair<Scene*, Request*>> batch;
+        std::vector<nm::GroupView> views;
+        size_t pixels = 0;
+        uint32_t stride = 0;
+        const size_t cap = std::max<uint32_t>(1, s->cfg.max_inflight);
+        for (auto& sc : s->scenes) {
+            if (!sc.active) continue;
+            nm::SceneView sv;
+            if (!nm::scene_view(sc.h, &sv) || sv.precision != prec) continue;
+            size_t taken = 0;
+            // a view larger than the batch budget goes alone
+            while (!sc.fifo.empty() && sc.fifo.front()->kind == MAP_REQ_RENDER && sc.inflight.size() + taken < cap &&
+                   (batch.empty() || pixels + (size_t)sc.fifo.front()->W * sc.fifo.front()->H <= kGroupMaxPixels)) {
+                Request* r = sc.fifo.front();
+                sc.fifo.pop_front();
+                batch.emplace_back(&sc, r);
+                nm::GroupView gv{};
+                gv.scene = sv;
+                std::memcpy(gv.c2w, r->c2w, sizeof(gv.c2w));
+                std::memcpy(gv.K, r->K, sizeof(gv.K));
+                gv.W = r->W;
+                gv.H = r->H;
+                views.push_back(gv);
+                pixels += (size_t)r->W * r->H;
+                stride = std::max(stride, sv.dc.max_samples);
+                ++taken;
+            }
+        }
+        if (batch.empty()) continue;
+        any = true;
+        int rc = MAP_OK;
+        if (!s->group_stream && cudaStreamCreateWithFlags(&s->group_stream, cudaStreamNonBlocking) != cudaSuccess)
+            rc = MAP_ECUDA;
+        if (rc == MAP_OK && s->gbufs.row_stride < stride) {
+            if (s->gbufs.items) {
+                cudaStreamSynchronize(s->group_stream);
+                nm::group_bufs_free(s->gbufs);
+            }
+            rc = nm::group_bufs_alloc(s->gbufs, kGroupCapRays, std::max<uint32_t>(stride, 128));
+        }
+        if (rc == MAP_OK && s->arena_floats < 4 * pixels) {
+            cudaStreamSynchronize(s->group_stream);
+            cudaFree(s->arena);
+            s->arena = nullptr;
+            s->arena_floats = 0;
+            if (cudaMalloc((void**)&s->arena, 4 * pixels * sizeof(float)) != cudaSuccess) {
+                cudaGetLastError();
+                rc = MAP_ENOMEM;
+            } else {
+                s->arena_floats = 4 * pixels;
+            }
+        }
+        std::vector<Scene*> scenes;
+        for (auto& br : batch)
+            if (std::find(scenes.begin(), scenes.end(), br.first) == scenes.end()) scenes.push_back(br.first);
+        if (rc == MAP_OK) {
+            for (Scene* sc : scenes) {  // the render sees each scene as its queue left it
+                cudaEvent_t e = s->get_event();
+                cudaEventRecord(e, sc->stream);
+                cudaStreamWaitEvent(s->group_stream, e, 0);
+                s->event_pool.push_back(e);
+            }
+            size_t off = 0;
+            for (size_t k = 0; k < views.size(); ++k) {
+                const size_t n = (size_t)views[k].W * views[k].H;
+                views[k].out_rgb = s->arena + off;
+                views[k].out_depth = s->arena + off + 3 * n;
+                off += 4 * n;
+            }
+            const double t = s->now();
+            rc = nm::render_group(views.data(), (uint32_t)views.size(), prec == MAP_PREC_BF16, s->gbufs, s->n_sm,
+                                  s->group_stream, nullptr);
+            for (size_t k = 0; k < batch.size() && rc == MAP_OK; ++k) {
+                Request* r = batch[k].second;
+                const size_t n = (size_t)r->W * r->H;
+                cudaMemcpyAsync(r->pin_ptr, views[k].out_rgb, 4 * n * sizeof(float), cudaMemcpyDeviceToHost,
+                                s->group_stream);
+                r->t_start = t;
+                r->grouped = true;
+            }
+        }
+        if (rc != MAP_OK) {
+            for (auto& br : batch) {
+                s->release_pin(br.second);
+                complete(s, br.second, rc);
+            }
+            continue;
+        }
+        for (auto& br : batch) {
+            Request* r = br.second;
+            r->ev = s->get_event();
+            cudaEventRecord(r->ev, s->group_stream);
+            br.first->inflight.push_back(r);
+        }
+        cudaEvent_t done = s->get_event();
+        cudaEventRecord(done, s->group_stream);
+        for (Scene* sc : scenes) cudaStreamWaitEvent(sc->stream, done, 0);  // later steps wait for the render
+        s->event_pool.push_back(done);
+        s->grouped_renders += batch.size();
+        s->group_batches += 1;
+    }
+    return any;
+}
+
 bool issue(map_server_s* s, Scene& sc) {
     bool any = false;
     const size_t cap = std::max<uint32_t>(1, s->cfg.max_inflight);
     while (!sc.fifo.empty() && sc.inflight.size() < cap) {
         Request* r = sc.fifo.front();
+        // a tensor-core scene's render waits at the head of its queue for the next
+        // grouped render (issue_group), which keeps the scene's request order
+        if (s->cfg.group_renders && r->kind == MAP_REQ_RENDER && sc.precision != MAP_PREC_FP32) break;
         sc.fifo.pop_front();
         issue_one(s, sc, r);
         any = true;
@@ -270,11 +398,11 @@ void worker_main(map_server_s* s) {
             }
         }
         bool progress = false;
-        for (auto& sc : s->scenes) {
-            if (!sc.active) continue;
-            progress |= retire(s, sc);
-            progress |= issue(s, sc);
-        }
+        for (auto& sc : s->scenes)
+            if (sc.active) progress |= retire(s, sc);
+        if (s->cfg.group_renders) progress |= issue_group(s);
+        for (auto& sc : s->scenes)
+            if (sc.active) progress |= issue(s, sc);
         if (!progress) {
             std::unique_lock<std::mutex> lock(s->mu);
             if (s->incoming.empty()) s->cv.wait_for(lock, std::chrono::microseconds(50));
@@ -323,6 +451,7 @@ int map_server_create(const map_server_config* cfg, map_server* out) {
     map_server_s* s = new map_server_s();
     s->cfg = *cfg;
     cudaGetDevice(&s->device);
+    cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
     s->t0 = Clock::now();
     s->scenes.resize(cfg->max_scenes);
     s->worker = std::thread(worker_main, s);
@@ -348,6 +477,9 @@ int map_server_destroy(map_server s) {
         cudaStreamDestroy(sc.stream);
         cudaFree(sc.d_render);
     }
+    if (s->gbufs.items) nm::group_bufs_free(s->gbufs);
+    cudaFree(s->arena);
+    if (s->group_stream) cudaStreamDestroy(s->group_stream);
     for (Request* r : s->incoming) delete r;
     for (Request* r : s->done) delete r;
     for (auto& b : s->pins) cudaFreeHost(b.p);
@@ -388,6 +520,7 @@ int map_server_add_scene(map_server s, const map_config* cfg, int continuous_map
     sc.step_rays = s->cfg.step_rays;
     sc.seed = cfg->seed;  // the scene's own draws, whatever slot it lands in
     sc.mapping = continuous_mapping != 0;
+    sc.precision = cfg->precision;
     sc.footprint = need;
     sc.active = true;
     *scene_id = slot;
@@ -514,6 +647,8 @@ int map_server_get_stats(map_server s, map_server_stats* out) {
         out->device_bytes += sc.footprint;
     }
     out->pending = (uint32_t)(s->incoming.size() + s->done.size());
+    out->grouped_renders = s->grouped_renders.load();
+    out->group_batches = s->group_batches.load();
     return MAP_OK;
 }
 
