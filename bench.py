@@ -806,8 +806,7 @@ def main():
     render_ms = r0.elapsed_time(r1) / nv
     render_mpx = W * H / (render_ms / 1e3) / 1e6 * world
     render = render_roofline(cfg, rprof, nv, render_samples / nv, W * H, render_ms, args.precision)
-    render["value"] = render_mpx
-    render["unit"] = "Mpx/s"
+    render["mpx_s"] = render_mpx
 
     # ---------------- occupancy refresh (a13, every 16 steps in a mapping run): its cost
     # per refresh and amortised over 16 steps, beside the headline step

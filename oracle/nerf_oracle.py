@@ -551,7 +551,32 @@ def forward_backward(cfg, P, keyframes, n_rays, seed, step, occ_bits=None,
         ga, dfa = field_backward(P, fw, dsa, dra, magnitude=True)
         ga["tables"] = hash_backward(cfg, idx, wts, dfa)
         out["grads_abs"] = ga
+        near = near_kink_samples(P, fw)
+        touched = np.zeros((cfg.n_levels, cfg.table_size), bool)
+        for l in range(cfg.n_levels):
+            touched[l, idx[near, l, :].ravel()] = True
+        out["near_kink"] = near
+        out["near_kink_entries"] = touched
     return out
+
+
+# A ReLU branch (and the density cap) is an integer decided by floating point: where
+# a pre-activation lies within a rounding of zero, an FP32 evaluation may take the
+# other branch than FP64, and the sample's whole contribution to the gradient
+# changes; both results are correct evaluations of the method.  These samples are
+# found from the sum of the absolute values of each pre-activation's terms.
+KINK_TOL = 1e-5
+
+
+def near_kink_samples(P: dict, fw: dict, tol: float = KINK_TOL) -> np.ndarray:
+    """Samples with some ReLU pre-activation a satisfying |a| <= tol * sum|terms of a|
+    (or with h_0 within tol of the density cap): bool [S]."""
+    A = {k: np.abs(P[k].astype(np.float64)) for k in ("W1", "W3", "W4")}
+    near = np.any(np.abs(fw["a1"]) <= tol * (np.abs(fw["feat"]) @ A["W1"].T), axis=1)
+    near |= np.any(np.abs(fw["a3"]) <= tol * (np.abs(fw["x3"]) @ A["W3"].T), axis=1)
+    near |= np.any(np.abs(fw["a4"]) <= tol * (np.abs(fw["h3"]) @ A["W4"].T), axis=1)
+    near |= np.abs(fw["h"][:, 0] - SIGMA_H_MAX) <= tol * SIGMA_H_MAX
+    return near
 
 
 def loss_only(cfg, P, keyframes, n_rays, seed, step, occ_bits=None, level_res=None, rays=None):

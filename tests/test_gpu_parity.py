@@ -45,12 +45,18 @@ def _rel(a, b):
 
 
 def _check_grads(g_gpu, ref, rel=REL, elem=REL):
+    """Per-tensor relative L2, and element-wise against grads_abs except for the table
+    entries touched by samples with a ReLU pre-activation within 1e-5 of zero relative
+    to its terms (oracle.near_kink_samples): there FP32 and FP64 may take different
+    branches, and both results are correct; those entries stay under the L2 bound."""
     for k in ("tables", "W1", "W2", "W3", "W4", "W5"):
         a = np.asarray(g_gpu[k], np.float64)
         b = ref["grads"][k]
         assert _rel(a, b) <= rel, (k, _rel(a, b))
         tol = elem * ref["grads_abs"][k] + 1e-30
         bad = np.abs(a - b) > tol
+        if k == "tables":
+            bad &= ~ref["near_kink_entries"][:, :, None]
         assert not bad.any(), (k, int(bad.sum()), float((np.abs(a - b)[bad] / tol[bad]).max()))
 
 

@@ -554,6 +554,29 @@ def test_mlp_precision_floor_on_the_c1_step():
     assert all(floor["bf16"][k] > floor["fp16"][k] for k in floor["fp16"])
 
 
+def test_near_kink_samples_flag_pre_activations_at_zero():
+    """near_kink_samples flags a sample exactly when one of its ReLU pre-activations
+    (or h_0 against the density cap) is within the tolerance of zero relative to the
+    sum of its terms' magnitudes: built here with one unit cancelling exactly, one
+    just outside the tolerance and one sample far from every kink."""
+    shapes = {"W1": (64, 32), "W2": (16, 64), "W3": (64, 32), "W4": (64, 64), "W5": (3, 64)}
+    P = {k: np.zeros(s) for k, s in shapes.items()}
+    P["W1"][:, 0] = 1.0                                   # every layer-1 unit = f0 + ...
+    P["W1"][0, 1] = -1.0                                  # ... unit 0 = f0 - f1
+    feat = np.zeros((3, 32))
+    feat[:, 0] = 1.0
+    feat[0, 1] = 1.0                                      # sample 0: unit 0 is exactly 0
+    feat[1, 1] = 1.0 - 3e-5                               # sample 1: |a| = 3e-5, terms sum to ~2
+    feat[2, 1] = -1.0                                     # sample 2: unit 0 = 2
+    sh = np.zeros((3, 16))
+    sh[:, 0] = 1.0
+    P["W3"][:, 16] = 1.0                                  # layer-3 units = sh_0 = 1: no kink
+    P["W4"][:, 0] = 1.0
+    fw = oracle.field_forward(P, feat, sh)
+    assert list(oracle.near_kink_samples(P, fw)) == [True, False, False]
+    assert list(oracle.near_kink_samples(P, fw, tol=2e-5)) == [True, True, False]
+
+
 def test_density_cap_is_opaque_and_flat():
     """sigma = exp(min(h_0, 15)): above the cap the value is exp(15) and the loss
     does not depend on h_0 (zero derivative, checked by central differences)."""
