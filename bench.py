@@ -53,6 +53,10 @@ def parse():
     p.add_argument("--ablation", action="store_true", help="also run the Sigma_D-weighting ablation (about 1 min)")
     p.add_argument("--quality-full", action="store_true",
                    help="run only the full-size training-quality comparison (about 10 min) and print its JSON")
+    p.add_argument("--quality-sigma-floor", type=float, default=0.0,
+                   help="lower bound (m) of the keyframes' depth-noise sigma_d in the quality comparison")
+    p.add_argument("--quality-precisions", default="fp32,fp16,bf16")
+    p.add_argument("--quality-seeds", default="0,1,2")
     p.add_argument("--serving-seconds", type=float, default=6.0)
     p.add_argument("--rays", type=int, default=N_RAYS)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -219,6 +223,7 @@ def quality_workload(n_poses=60, every=6, kf_W=320, kf_H=240, view_W=160, view_H
     rendered analytically at view_W x view_H without noise; the others become
     kf_W x kf_H keyframes with depth noise sigma_d = max(0.01 z^2 U[0.5, 2],
     sigma_floor) (and `outlier_frac` of gross depth errors reported with sigma_d = 1 m)."""
+    import numpy as np
     import synth
     room = synth.make_room(seed)
     poses = synth.room_spline_poses(room, n_poses, seed=seed + 5)
@@ -230,7 +235,13 @@ def quality_workload(n_poses=60, every=6, kf_W=320, kf_H=240, view_W=160, view_H
     Kv = (525.0 * view_W / 640, 525.0 * view_H / 480, view_W / 2.0, view_H / 2.0)
     views = synth.room_keyframes(room, len(held), seed=seed + 9, W=view_W, H=view_H, K=Kv, noise_k=0.0,
                                  poses=[poses[i] for i in sorted(held)])
-    return {"room": room, "kfs": kfs, "views": views, "seed": seed, "view_wh": (view_W, view_H)}
+    # five training poses rendered like the held-out views: how well the fit
+    # reproduces what it was trained on, beside how well it generalises
+    tsel = [train[k] for k in np.linspace(0, len(train) - 1, 5).astype(int)]
+    train_views = synth.room_keyframes(room, len(tsel), seed=seed + 11, W=view_W, H=view_H, K=Kv, noise_k=0.0,
+                                       poses=tsel)
+    return {"room": room, "kfs": kfs, "views": views, "train_views": train_views, "seed": seed,
+            "view_wh": (view_W, view_H), "sigma_floor": sigma_floor}
 
 
 def quality_fit(wl, precision, steps, rays, ray_seed=0, depth_weighting="sigma_d"):
@@ -265,9 +276,9 @@ def quality_fit(wl, precision, steps, rays, ray_seed=0, depth_weighting="sigma_d
     for kf in kfs:
         m.add_keyframe(kf)
 
-    def evaluate():
+    def evaluate(which="views"):
         ps, dl = [], []
-        for v in wl["views"]:
+        for v in wl[which]:
             rgb, dep, _ = m.render(v.c2w, v.K, W, H)
             uu, vv = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
             s = np.sqrt(((uu - v.K[2]) / v.K[0]) ** 2 + ((vv - v.K[3]) / v.K[1]) ** 2 + 1.0)
@@ -285,10 +296,12 @@ def quality_fit(wl, precision, steps, rays, ray_seed=0, depth_weighting="sigma_d
     loss = m.step(rays, seed=ray_seed, no_update=True)
     t = time.perf_counter() - t0
     p1, d1 = evaluate()
+    pt, dt = evaluate("train_views")
     m.close()
     return {"precision": precision, "steps": steps, "rays_per_step": rays, "train_keyframes": len(kfs),
             "depth_weighting": depth_weighting, "heldout_views": len(wl["views"]), "psnr_db": p1,
-            "depth_l1_m": d1, "psnr_db_init": p0, "depth_l1_m_init": d0, "final_loss": loss, "train_s": t}
+            "depth_l1_m": d1, "psnr_db_init": p0, "depth_l1_m_init": d0, "train_view_psnr_db": pt,
+            "train_view_depth_l1_m": dt, "final_loss": loss, "train_s": t, "sigma_floor": wl["sigma_floor"]}
 
 
 def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, H=120, seed=0,
@@ -302,7 +315,7 @@ def quality_run(precision, steps=600, rays=1 << 16, n_poses=60, every=6, W=160, 
     return r
 
 
-def quality_full(precisions=("fp32", "fp16", "bf16"), seeds=(0, 1, 2), steps=2000, rays=1 << 18):
+def quality_full(precisions=("fp32", "fp16", "bf16"), seeds=(0, 1, 2), steps=2000, rays=1 << 18, sigma_floor=0.0):
     """The training configuration at its stated size: 100 keyframes of 640x480 along
     the seeded spline (110 poses, every 11th held out: 10 held-out 640x480 views),
     depth noise sigma_d = 0.01 z^2 U[0.5, 2] with no floor, `steps` steps of `rays`
@@ -310,9 +323,11 @@ def quality_full(precisions=("fp32", "fp16", "bf16"), seeds=(0, 1, 2), steps=200
     same initial parameters; PSNR / depth-L1 per fit and per-form means."""
     import statistics as st
     t0 = time.perf_counter()
-    wl = quality_workload(n_poses=110, every=11, kf_W=640, kf_H=480, view_W=640, view_H=480, sigma_floor=0.0)
+    wl = quality_workload(n_poses=110, every=11, kf_W=640, kf_H=480, view_W=640, view_H=480,
+                          sigma_floor=sigma_floor)
     out = {"workload": "room, 100 keyframes 640x480 on a seeded spline, 10 held-out 640x480 views, "
-                       f"{steps} steps of {rays} rays", "generation_s": time.perf_counter() - t0, "fits": []}
+                       f"{steps} steps of {rays} rays, depth noise sigma_d = max(0.01 z^2 U[0.5,2], {sigma_floor} m)",
+           "generation_s": time.perf_counter() - t0, "fits": []}
     for prec in precisions:
         for sd in seeds:
             out["fits"].append(quality_fit(wl, prec, steps, rays, ray_seed=sd))
@@ -321,6 +336,7 @@ def quality_full(precisions=("fp32", "fp16", "bf16"), seeds=(0, 1, 2), steps=200
         ps, dl = [f["psnr_db"] for f in fs], [f["depth_l1_m"] for f in fs]
         out[prec] = {"psnr_db_mean": st.mean(ps), "psnr_db_sd": st.stdev(ps) if len(ps) > 1 else 0.0,
                      "depth_l1_m_mean": st.mean(dl), "depth_l1_m_sd": st.stdev(dl) if len(dl) > 1 else 0.0,
+                     "train_view_psnr_db_mean": st.mean(f["train_view_psnr_db"] for f in fs),
                      "train_s_mean": st.mean(f["train_s"] for f in fs)}
     return out
 
@@ -685,7 +701,10 @@ def main():
         torch.cuda.set_device(local)
         import __graft_entry__
         __graft_entry__.build()
-        print(json.dumps({"quality_full": quality_full(steps=args.steps if args.steps != 20 else 2000)}), flush=True)
+        print(json.dumps({"quality_full": quality_full(
+            precisions=tuple(args.quality_precisions.split(",")),
+            seeds=tuple(int(x) for x in args.quality_seeds.split(",")),
+            steps=args.steps if args.steps != 20 else 2000, sigma_floor=args.quality_sigma_floor)}), flush=True)
         return
 
     if args.only_large_map:

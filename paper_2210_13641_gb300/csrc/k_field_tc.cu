@@ -195,8 +195,8 @@ constexpr int kT32 = 128 * 32 * 2, kT64 = 128 * 64 * 2, kT16 = 128 * 16 * 2;
 constexpr int kFwdSmem = kWB + kT32 + kT64;                            // 45056
 
 // ------------------------------------------------------------------ forward
-// One tile of the forward: samples i0 .. i0 + count - 1 (count <= 128); thread r of
-// the block owns sample row r.  smem: the weight tiles, then tA (128 x 32: X0, X3) and
+// One tile of the forward: samples i0 .. min(i0 + 128, i_end) - 1; thread r of the
+// block owns sample row r.  smem: the weight tiles, then tA (128 x 32: X0, X3) and
 // tB (128 x 64: H1, H3, H4; a layer's MMAs have completed before its output
 // overwrites its input).  Returns after the tile's last MMA wait.
 template <bool BF16>
@@ -204,7 +204,7 @@ __device__ __forceinline__ void fwd_tile(const DevCfg& c, const float2* __restri
                                          const float* __restrict__ rays, uint32_t cap,
                                          const uint32_t* __restrict__ ray_id, const float* __restrict__ ts,
                                          float4* __restrict__ sig_rgb, uint4* __restrict__ feat_out,
-                                         float feat_scale, uint32_t i0, uint32_t count, uint8_t* smem,
+                                         float feat_scale, uint32_t i0, uint32_t i_end, uint8_t* smem,
                                          uint32_t tmem, uint64_t* bar, uint32_t& phase, bool& timed_out) {
     uint8_t* sW1 = smem;
     uint8_t* sW2 = sW1 + kW1B;
@@ -217,7 +217,7 @@ __device__ __forceinline__ void fwd_tile(const DevCfg& c, const float2* __restri
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     const float inv_fs = 1.f / feat_scale;
     const uint32_t i = i0 + tid;
-    const bool valid = (uint32_t)tid < count;
+    const bool valid = i < i_end;
     float v[32];
     float3 d = make_float3(0.f, 0.f, 0.f);
     float3 x = make_float3(0.f, 0.f, 0.f);
@@ -353,8 +353,8 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
     bool timed_out = false;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t i0 = tile * 128;
-        fwd_tile<BF16>(c, tables, rays, cap, ray_id, ts, sig_rgb, feat_out, feat_scale, i0, min(128u, n - i0), smem,
-                       tmem, &bar, phase, timed_out);
+        fwd_tile<BF16>(c, tables, rays, cap, ray_id, ts, sig_rgb, feat_out, feat_scale, i0, n, smem, tmem, &bar, phase,
+                       timed_out);
         fence_before_sync();
         if (__syncthreads_or(timed_out)) {
             if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(128, 4) k_group_fwd_tc(const GroupItem* __rest
         }
         const uint32_t k = (tile - tile0_s[j]) * 128;
         fwd_tile<BF16>(cfg_s, reinterpret_cast<const float2*>(it.params), rays, cap, ray_id, ts, sig_rgb, nullptr,
-                       feat_scale, it.s0 + k, min(128u, it.n_s - k), smem, tmem, &bar, phase, timed_out);
+                       feat_scale, it.s0 + k, it.s0 + it.n_s, smem, tmem, &bar, phase, timed_out);
         fence_before_sync();
         if (__syncthreads_or(timed_out)) {
             if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
