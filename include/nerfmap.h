@@ -405,9 +405,9 @@ int map_march_noalloc(const map_config* cfg, const uint8_t* occ_bits, const floa
  * tensor-core field forward whose 128-sample tiles never mix two views and which
  * switches weights where the scene changes, compositing, output).  Every pixel goes
  * through the arithmetic of a render of its view alone, so the results are the same
- * bit for bit.  The grouped render runs on the server's own stream after the work
- * each scene has already queued, and each scene's later work waits for it.  Plain
- * FP32 scenes render on their own streams.
+ * bit for bit.  A grouped render runs on one of the server's two render streams
+ * (taken in turn) after the work each scene has already queued, and each scene's
+ * later work waits for it.  Plain FP32 scenes render on their own streams.
  */
 typedef struct map_server_s* map_server;
 

@@ -96,11 +96,18 @@ struct map_server_s {
     std::atomic<bool> stop{false};
     std::thread worker;
     std::atomic<uint64_t> rays_done{0};
-    // grouped renders (cfg.group_renders): their stream, work buffers and output arena
-    cudaStream_t group_stream = nullptr;
-    nm::GroupBufs gbufs{};
-    float* arena = nullptr;
-    size_t arena_floats = 0;
+    // grouped renders (cfg.group_renders): lanes of a stream, work buffers and an
+    // output arena each, taken in turn, so that batches issued one after the other
+    // (lone renders of different scenes, the usual case) still overlap on the device
+    struct GroupLane {
+        cudaStream_t stream = nullptr;
+        nm::GroupBufs gbufs{};
+        float* arena = nullptr;
+        size_t arena_floats = 0;
+    };
+    static constexpr int kGroupLanes = 2;
+    GroupLane lanes[kGroupLanes];
+    int next_lane = 0;
     int n_sm = 0;
     std::atomic<uint64_t> grouped_renders{0}, group_batches{0};
 
@@ -215,9 +222,9 @@ constexpr uint32_t kGroupCapRays = 1u << 18;
 constexpr size_t kGroupMaxPixels = (size_t)1 << 22;  // pixels of one grouped batch
 
 // Renders at the head of the tensor-core scenes' queues, issued together: one grouped
-// render (shared launches over all their views) per MLP type on the group stream,
-// which first waits for the work each scene has already queued; each scene's later
-// work waits for the grouped render (it reads the scene's parameters).  Returns
+// render (shared launches over all their views) per MLP type on the next group lane's
+// stream, which first waits for the work each scene has already queued; each scene's
+// later work waits for the grouped render (it reads the scene's parameters).  Returns
 // whether anything was issued.
 bool issue_group(map_server_s* s) {
     bool any = false;
@@ -252,26 +259,28 @@ bool issue_group(map_server_s* s) {
         }
         if (batch.empty()) continue;
         any = true;
+        map_server_s::GroupLane& L = s->lanes[s->next_lane];
+        s->next_lane = (s->next_lane + 1) % map_server_s::kGroupLanes;
         int rc = MAP_OK;
-        if (!s->group_stream && cudaStreamCreateWithFlags(&s->group_stream, cudaStreamNonBlocking) != cudaSuccess)
+        if (!L.stream && cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess)
             rc = MAP_ECUDA;
-        if (rc == MAP_OK && s->gbufs.row_stride < stride) {
-            if (s->gbufs.items) {
-                cudaStreamSynchronize(s->group_stream);
-                nm::group_bufs_free(s->gbufs);
+        if (rc == MAP_OK && L.gbufs.row_stride < stride) {
+            if (L.gbufs.items) {
+                cudaStreamSynchronize(L.stream);
+                nm::group_bufs_free(L.gbufs);
             }
-            rc = nm::group_bufs_alloc(s->gbufs, kGroupCapRays, std::max<uint32_t>(stride, 128));
+            rc = nm::group_bufs_alloc(L.gbufs, kGroupCapRays, std::max<uint32_t>(stride, 128));
         }
-        if (rc == MAP_OK && s->arena_floats < 4 * pixels) {
-            cudaStreamSynchronize(s->group_stream);
-            cudaFree(s->arena);
-            s->arena = nullptr;
-            s->arena_floats = 0;
-            if (cudaMalloc((void**)&s->arena, 4 * pixels * sizeof(float)) != cudaSuccess) {
+        if (rc == MAP_OK && L.arena_floats < 4 * pixels) {
+            cudaStreamSynchronize(L.stream);
+            cudaFree(L.arena);
+            L.arena = nullptr;
+            L.arena_floats = 0;
+            if (cudaMalloc((void**)&L.arena, 4 * pixels * sizeof(float)) != cudaSuccess) {
                 cudaGetLastError();
                 rc = MAP_ENOMEM;
             } else {
-                s->arena_floats = 4 * pixels;
+                L.arena_floats = 4 * pixels;
             }
         }
         std::vector<Scene*> scenes;
@@ -281,24 +290,24 @@ bool issue_group(map_server_s* s) {
             for (Scene* sc : scenes) {  // the render sees each scene as its queue left it
                 cudaEvent_t e = s->get_event();
                 cudaEventRecord(e, sc->stream);
-                cudaStreamWaitEvent(s->group_stream, e, 0);
+                cudaStreamWaitEvent(L.stream, e, 0);
                 s->event_pool.push_back(e);
             }
             size_t off = 0;
             for (size_t k = 0; k < views.size(); ++k) {
                 const size_t n = (size_t)views[k].W * views[k].H;
-                views[k].out_rgb = s->arena + off;
-                views[k].out_depth = s->arena + off + 3 * n;
+                views[k].out_rgb = L.arena + off;
+                views[k].out_depth = L.arena + off + 3 * n;
                 off += 4 * n;
             }
             const double t = s->now();
-            rc = nm::render_group(views.data(), (uint32_t)views.size(), prec == MAP_PREC_BF16, s->gbufs, s->n_sm,
-                                  s->group_stream, nullptr);
+            rc = nm::render_group(views.data(), (uint32_t)views.size(), prec == MAP_PREC_BF16, L.gbufs, s->n_sm,
+                                  L.stream, nullptr);
             for (size_t k = 0; k < batch.size() && rc == MAP_OK; ++k) {
                 Request* r = batch[k].second;
                 const size_t n = (size_t)r->W * r->H;
                 cudaMemcpyAsync(r->pin_ptr, views[k].out_rgb, 4 * n * sizeof(float), cudaMemcpyDeviceToHost,
-                                s->group_stream);
+                                L.stream);
                 r->t_start = t;
                 r->grouped = true;
             }
@@ -313,11 +322,11 @@ bool issue_group(map_server_s* s) {
         for (auto& br : batch) {
             Request* r = br.second;
             r->ev = s->get_event();
-            cudaEventRecord(r->ev, s->group_stream);
+            cudaEventRecord(r->ev, L.stream);
             br.first->inflight.push_back(r);
         }
         cudaEvent_t done = s->get_event();
-        cudaEventRecord(done, s->group_stream);
+        cudaEventRecord(done, L.stream);
         for (Scene* sc : scenes) cudaStreamWaitEvent(sc->stream, done, 0);  // later steps wait for the render
         s->event_pool.push_back(done);
         s->grouped_renders += batch.size();
@@ -477,9 +486,11 @@ int map_server_destroy(map_server s) {
         cudaStreamDestroy(sc.stream);
         cudaFree(sc.d_render);
     }
-    if (s->gbufs.items) nm::group_bufs_free(s->gbufs);
-    cudaFree(s->arena);
-    if (s->group_stream) cudaStreamDestroy(s->group_stream);
+    for (auto& L : s->lanes) {
+        if (L.gbufs.items) nm::group_bufs_free(L.gbufs);
+        cudaFree(L.arena);
+        if (L.stream) cudaStreamDestroy(L.stream);
+    }
     for (Request* r : s->incoming) delete r;
     for (Request* r : s->done) delete r;
     for (auto& b : s->pins) cudaFreeHost(b.p);
