@@ -545,18 +545,21 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # FP16 tensor-core field kernels on this workload (2^18 rays, 15,869,619 samples),
-# from one ncu capture of `python bench.py --steps 2 --warmup 1 --no-cpu-baseline
-# --no-forms --no-serving --no-large-map` with those two metrics (one pass).  Valid only while the
-# kernel sources are the ones captured: the digest of the files below must match.
+# from one ncu capture of the second timed step of `python bench.py --steps 2 --warmup 1
+# --no-cpu-baseline --no-forms --no-serving --no-large-map` with those metrics (one
+# pass), and the tensor pipe's and the L2's activity from one launch of the 32768-ray
+# case of the same command.  Valid only while the kernel sources are the ones captured:
+# the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
-    "sha256": "ea610a94cbb14858b229bda7e5982da77fe79d973e595c2b6ba12362664e7adc",
+    "sha256": "9bc920bae7ae00575f90446673242bf4e8e7636fb603899305c6078c6d4a55cb",
     "samples": 15869619,
-    "field_fwd": 312883968 + 1244670208,
-    "field_bwd": 1720428288 + 208510720,
-    # sm__pipe_tensor_cycles_active (share of peak, elapsed) of one launch on the
-    # 32768-ray case (ncu --metrics sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed)
-    "tensor_pipe": {"field_fwd": 0.0352, "field_bwd": 0.0812},
+    "field_fwd": 295702016 + 1240706048,
+    "field_bwd": 1719796736 + 207590144,
+    # sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed and
+    # lts__throughput.avg.pct_of_peak_sustained_elapsed of one launch on the 32768-ray case
+    "tensor_pipe": {"field_fwd": 0.0373, "field_bwd": 0.0815},
+    "lts_throughput": {"field_fwd": 0.3272, "field_bwd": 0.5479},
 }
 
 
@@ -614,8 +617,10 @@ def roofline(cfg, prof, n_samples, n_params, precision):
     for k, peak_key in (("field_fwd", "stream_read_gbs"), ("field_bwd", "stream_reduce_gbs")):
         ach = table_bytes / (cand[k] / 1e3) / 1e9
         tr = measured_traffic(k, precision, n_samples)
+        lts = (NCU_TRAFFIC["lts_throughput"][k] if precision == "fp16" and
+               kernel_sources_digest() == NCU_TRAFFIC["sha256"] else None)
         kernels[k] = {"bound": "l2", "achieved": ach, "peak": l2[peak_key], "unit": "GB/s",
-                      "frac": ach / l2[peak_key], "ms": cand[k],
+                      "frac": ach / l2[peak_key], "ms": cand[k], "ncu_lts_throughput": lts,
                       "frac_of_random_ceiling": ach / l2["random_read_gbs" if k == "field_fwd" else "random_reduce_gbs"],
                       "hbm": {"traffic": tr, "achieved": None if tr is None else tr / (cand[k] / 1e3) / 1e9,
                               "peak": hbm, "frac": None if tr is None else tr / (cand[k] / 1e3) / 1e9 / hbm}}
