@@ -9,7 +9,10 @@ that scatters by about 1.2 %.  So each form is fitted with three ray seeds and t
 means are compared: the FP16 mean may fall short of the FP32 mean by at most 0.5 dB
 in PSNR and 3 % in depth-L1 (twice the scatter of a difference of two 3-run means;
 ending better is no failure), the BF16 mean (8 significand bits) by at most 1 dB and
-5 %.  The FP16 form must also train in at most 35 % of the FP32 time.  The measured
+5 %.  The FP16 form must also train in at most 35 % of the FP32 time.  The north
+star's +-0.1 dB is below what three seeds resolve here (the spread above); the
+full-size comparison (bench.py --quality-full: 100 keyframes of 640x480, 2000 steps
+of 2^18 rays) measures a per-fit spread of 0.1-0.8 dB as well.  The measured
 numbers are appended to NERFMAP_QUALITY_REPORT (JSON lines) when that is set."""
 
 import json
