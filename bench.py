@@ -642,18 +642,19 @@ def roofline(cfg, prof, n_samples, n_params, precision):
     return roof
 
 
-def render_roofline(cfg, rprof, n_views, samples_per_view, pixels, ms_per_view, precision):
-    """Roofline of a render: its forward field kernel gathers 8 corners x L levels
-    x F features x 4 B per retained sample (early termination is applied in the
-    compositing, after the forward), against the L2 streaming read bandwidth."""
+def render_roofline(cfg, rprof, n_views, samples_per_view, evaluated_per_view, pixels, ms_per_view, precision):
+    """Roofline of a render: its field forward gathers 8 corners x L levels x F
+    features x 4 B per evaluated sample (with early termination a render evaluates the
+    first 32 samples of every ray and then only the rays still above the threshold),
+    against the L2 streaming read bandwidth."""
     l2 = l2_ceilings(cfg)
     fwd_ms = rprof["field_fwd"]["ms"] / n_views
-    table_bytes = samples_per_view * 8 * cfg.n_levels * cfg.n_features * 4
+    table_bytes = evaluated_per_view * 8 * cfg.n_levels * cfg.n_features * 4
     ach = table_bytes / (fwd_ms / 1e3) / 1e9
     return {"kernel": "field_fwd", "bound": "l2", "achieved": ach, "peak": l2["stream_read_gbs"], "unit": "GB/s",
             "frac": ach / l2["stream_read_gbs"], "ms_per_view": ms_per_view, "field_fwd_ms_per_view": fwd_ms,
-            "samples_per_pixel": samples_per_view / pixels, "pixels": pixels,
-            "phase_ms_per_view": {k: v["ms"] / n_views for k, v in rprof.items() if v["count"]}}
+            "samples_per_pixel": samples_per_view / pixels, "evaluated_per_pixel": evaluated_per_view / pixels,
+            "pixels": pixels, "phase_ms_per_view": {k: v["ms"] / n_views for k, v in rprof.items() if v["count"]}}
 
 
 def kernel_sources_digest():
@@ -811,26 +812,35 @@ def main():
         m.render(kfs[i].c2w, kfs[i].K, W, H, out_rgb=out, out_depth=dep, stream=stream)
     torch.cuda.synchronize()
     nv = max(args.steps, 5)
-    render_samples = 0
-    for i in range(nv):                                   # retained samples of each timed view
-        k = kfs[i % len(kfs)]
-        m.render(k.c2w, k.K, W, H, out_rgb=out, out_depth=dep, stream=stream)
-        render_samples += m.stats().render_samples
-    m.profile(True)
-    r0 = torch.cuda.Event(enable_timing=True)
-    r1 = torch.cuda.Event(enable_timing=True)
-    r0.record(stream)
-    for i in range(nv):
-        k = kfs[i % len(kfs)]
-        m.render(k.c2w, k.K, W, H, out_rgb=out, out_depth=dep, stream=stream)
-    r1.record(stream)
-    torch.cuda.synchronize()
-    rprof = m.profile_read()
-    m.profile(False)
-    render_ms = r0.elapsed_time(r1) / nv
-    render_mpx = W * H / (render_ms / 1e3) / 1e6 * world
-    render = render_roofline(cfg, rprof, nv, render_samples / nv, W * H, render_ms, args.precision)
-    render["mpx_s"] = render_mpx
+
+    def time_renders():
+        """Mpx/s of nv 640x480 renders of the keyframe poses, with the retained and the
+        evaluated samples per view and the phase times."""
+        retained = evaluated = 0
+        for i in range(nv):                                   # sample counts of each timed view
+            k = kfs[i % len(kfs)]
+            m.render(k.c2w, k.K, W, H, out_rgb=out, out_depth=dep, stream=stream)
+            st = m.stats()
+            retained += st.render_samples
+            evaluated += st.render_evaluated
+        m.profile(True)
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        for i in range(nv):
+            k = kfs[i % len(kfs)]
+            m.render(k.c2w, k.K, W, H, out_rgb=out, out_depth=dep, stream=stream)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        rprof = m.profile_read()
+        m.profile(False)
+        rms = r0.elapsed_time(r1) / nv
+        r = render_roofline(cfg, rprof, nv, retained / nv, evaluated / nv, W * H, rms, args.precision)
+        r["mpx_s"] = W * H / (rms / 1e3) / 1e6 * world
+        return r
+
+    render = time_renders()
+    render_mpx = render["mpx_s"]
 
     # ---------------- occupancy refresh (a13, every 16 steps in a mapping run): its cost
     # per refresh and amortised over 16 steps, beside the headline step
@@ -845,12 +855,22 @@ def main():
     o1.record(stream)
     torch.cuda.synchronize()
     occ_ms = o0.elapsed_time(o1) / 3
+    m.set_occupancy(bits)                                 # back to the workload's bitfield
     step_ms = ms / args.steps
     occupancy = {"cells": cfg.occ_res ** 3, "ms_per_refresh": occ_ms, "refresh_every": 16,
                  "amortised_ms_per_step": occ_ms / 16,
                  "rays_per_s_with_refresh": n / ((step_ms + occ_ms / 16) / 1e3) * world,
                  "note": "one density evaluation (encoding + density MLP, FP32) per cell at a jittered point, "
                          "EMA and threshold; timed after the timed steps, outside them"}
+
+    # ---------------- render of a fitted map: 300 more mapping steps make the surfaces
+    # opaque, so rays stop early and the render evaluates fewer samples (two-pass render)
+    fit_steps = 300
+    for i in range(fit_steps):
+        m.step(n, seed=5000 + i, want_loss=False, stream=stream)
+    torch.cuda.synchronize()
+    render_fitted = time_renders()
+    render_fitted["fitted_steps"] = args.warmup + 2 * args.steps + fit_steps
 
     # ---------------- the other MLP precisions on the same workload (FP32 plain form, BF16)
     m.close()
@@ -905,7 +925,8 @@ def main():
                            "samples_per_step": n_samples, "mean_samples_per_ray": n_samples / n,
                            "l2": "working set > L2: params+grads+Adam moments (0.27 GB) streamed every step",
                            "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
-                "roofline": roof, "render_mpx_s": render_mpx, "render": render, "occupancy_refresh": occupancy,
+                "roofline": roof, "render_mpx_s": render_mpx, "render": render, "render_fitted": render_fitted,
+                "occupancy_refresh": occupancy,
                 "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "forms": forms}
         if serving:
             line["serving"] = serving

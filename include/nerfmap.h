@@ -130,6 +130,7 @@ typedef struct map_stats {
     uint64_t device_bytes;  /* device memory held by the map */
     uint64_t kernel_launches; /* kernels this map has launched since creation */
     uint64_t render_samples;  /* retained samples of the last map_render, all its chunks */
+    uint64_t render_evaluated; /* of those, the samples whose field the render evaluated */
 } map_stats;
 
 /* Phases of a step or render, for map_profile_read. */
@@ -215,7 +216,10 @@ const float* map_loss_device(map_handle h);
  * floats, out_depth: H*W floats (expected ray-termination distance along the unit
  * ray), both in mem_kind memory; either may be NULL.  out_acc (nullable, same
  * memory kind): H*W accumulated opacities.  Rays stop once transmittance drops
- * below cfg.render_t_min.  Views of more than max(2^18, the map's current ray
+ * below cfg.render_t_min; with render_t_min > 0 the field is evaluated for the
+ * first 32 samples of every ray and then only for the rays that have not stopped
+ * (the image equals that of evaluating every sample, bit for bit;
+ * map_stats.render_evaluated counts the evaluated samples).  Views of more than max(2^18, the map's current ray
  * capacity) pixels are rendered in chunks of that many pixels (map_get_samples and
  * map_get_ray_outputs then describe the last chunk).  With host outputs the call
  * waits for the stream; with device outputs it returns once the work is queued.

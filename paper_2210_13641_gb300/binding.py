@@ -54,7 +54,7 @@ class MapStats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_uint64), ("n_samples", ctypes.c_uint64), ("n_rays", ctypes.c_uint32),
                 ("n_keyframes", ctypes.c_uint32), ("param_count", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("render_samples", ctypes.c_uint64)]
+                ("render_samples", ctypes.c_uint64), ("render_evaluated", ctypes.c_uint64)]
 
 
 class ServerConfig(ctypes.Structure):

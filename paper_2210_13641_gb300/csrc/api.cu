@@ -75,6 +75,8 @@ struct map_scene {
     std::vector<PhaseRec> prof;
     std::string err;
     GroupBufs group{};              // work buffers of map_render_group calls led by this map
+    uint32_t* render_off = nullptr; // [cap_rays + 1] scan of a two-pass render's selection
+    uint32_t render_off_cap = 0;
 };
 
 namespace {
@@ -720,24 +722,59 @@ int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, 
     DevCfg dc = h->dc;
     dc.t_min = h->cfg.render_t_min;
     float* tmp = b.feat;  // host outputs: staged here (unused by a render), then copied
-    NM_CUDA(h, cudaMemsetAsync(render_sample_counter(b), 0, sizeof(unsigned long long), s));
+    NM_CUDA(h, cudaMemsetAsync(render_sample_counter(b), 0, 2 * sizeof(unsigned long long), s));
+    // Early termination saves field work: with a threshold the field is evaluated for
+    // the first kRenderFirst samples of every ray, then only for the rays whose
+    // transmittance is still above it (the images equal a single pass's bit for bit).
+    const bool two_pass = dc.t_min > 0.f;
+    if (two_pass && h->render_off_cap < b.cap_rays) {
+        cudaStreamSynchronize(s);
+        dfree(h, h->render_off);
+        h->render_off = nullptr;
+        h->render_off_cap = 0;
+        rc = dalloc(h, (void**)&h->render_off, (b.cap_rays + 1) * sizeof(uint32_t));
+        if (rc) return rc;
+        h->render_off_cap = b.cap_rays;
+    }
+    uint32_t* sel = reinterpret_cast<uint32_t*>(b.dsig_rgb);  // unused by a render: the selections
+    const bool fp32 = h->cfg.precision == MAP_PREC_FP32, bf16 = h->cfg.precision == MAP_PREC_BF16;
+    auto fwd_sel = [&](const uint32_t* n_sel) {
+        if (fp32) launch_field_fwd_fp32_sel(h->dc, h->params, sel, n_sel, b, h->n_sm, s);
+        else launch_field_fwd_tc_sel(h->dc, h->params, sel, n_sel, b, bf16, h->n_sm, s);
+    };
     for (uint32_t p0 = 0; p0 < n; p0 += chunk) {
         const uint32_t cnt = std::min(chunk, n - p0);
         rc = phase(h, MAP_PH_RAYGEN, 1, s, [&] { launch_ray_gen_view(c2w, K, W, p0, cnt, b, s); });
-        if (!rc) rc = run_forward(h, cnt, false, s);
-        if (!rc) rc = phase(h, MAP_PH_COMPOSITE, 1, s, [&] { launch_composite(dc, cnt, false, b, s); });
+        if (!two_pass) {
+            if (!rc) rc = run_forward(h, cnt, false, s);
+            if (!rc) rc = phase(h, MAP_PH_COMPOSITE, 1, s, [&] { launch_composite(dc, cnt, false, b, s); });
+        } else {
+            uint32_t* off = h->render_off;  // off[cnt]: the pass's total, read by the forward
+            if (!rc) rc = phase(h, MAP_PH_MARCH, 5, s, [&] { launch_march(h->dc, h->occ_bits, cnt, b, s); });
+            for (int pass = 1; pass <= 2 && !rc; ++pass) {
+                rc = phase(h, MAP_PH_FIELD_FWD, pass == 1 ? 6 : 5, s, [&] {
+                    launch_render_select(cnt, b.offsets, b.counts, pass == 1, kRenderFirst, off, b.block_sums, sel,
+                                         render_eval_counter(b), s);
+                    fwd_sel(off + cnt);
+                });
+                if (!rc)
+                    rc = phase(h, MAP_PH_COMPOSITE, 1, s,
+                               [&] { launch_composite_split(dc, cnt, pass, b.counts, b, s); });
+            }
+        }
         if (rc) return rc;
         h->last_rays = cnt;
         if (mem_kind == MAP_MEM_DEVICE) {
             rc = phase(h, MAP_PH_OUTPUT, 1, s, [&] {
                 launch_write_render(b, cnt, out_rgb ? out_rgb + 3 * (size_t)p0 : nullptr,
-                                    out_depth ? out_depth + p0 : nullptr, out_acc ? out_acc + p0 : nullptr, s);
+                                    out_depth ? out_depth + p0 : nullptr, out_acc ? out_acc + p0 : nullptr,
+                                    !two_pass, s);
             });
             if (rc) return rc;
             continue;
         }
         rc = phase(h, MAP_PH_OUTPUT, 1, s,
-                   [&] { launch_write_render(b, cnt, tmp, tmp + 3 * (size_t)cnt, tmp + 4 * (size_t)cnt, s); });
+                   [&] { launch_write_render(b, cnt, tmp, tmp + 3 * (size_t)cnt, tmp + 4 * (size_t)cnt, !two_pass, s); });
         if (rc) return rc;
         if (out_rgb)
             NM_CUDA(h, cudaMemcpyAsync(out_rgb + 3 * (size_t)p0, tmp, 3 * (size_t)cnt * sizeof(float),
@@ -932,9 +969,10 @@ int map_get_stats(map_handle h, map_stats* out) {
     out->param_count = h->n_params;
     out->device_bytes = h->held;
     out->kernel_launches = h->launches;
-    unsigned long long rs = 0;
-    if (h->bufs.loss) rc = copy_out(h, &rs, render_sample_counter(h->bufs), sizeof(rs), MAP_MEM_HOST, h->last_stream);
-    out->render_samples = rs;
+    unsigned long long rs[2] = {0, 0};
+    if (h->bufs.loss) rc = copy_out(h, rs, render_sample_counter(h->bufs), sizeof(rs), MAP_MEM_HOST, h->last_stream);
+    out->render_samples = rs[0];
+    out->render_evaluated = rs[1];
     return rc;
 }
 

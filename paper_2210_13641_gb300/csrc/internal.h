@@ -61,6 +61,27 @@ struct StepBufs {
 inline unsigned long long* render_sample_counter(const StepBufs& b) {
     return reinterpret_cast<unsigned long long*>(b.loss + 8);
 }
+// bytes 40..47 of the loss buffer: samples a render's field forward evaluated (all chunks)
+inline unsigned long long* render_eval_counter(const StepBufs& b) {
+    return reinterpret_cast<unsigned long long*>(b.loss + 10);
+}
+
+// ---------------------------------------------------------------- two-pass render
+// A render evaluates the field for the first kSplitFirst samples of every ray, then
+// only for the rays whose transmittance is still above the threshold (k_composite.cu).
+constexpr uint32_t kRenderFirst = 32;
+// k_rays.cu: the selection of a pass's samples.  first_pass: count[r] = min(first,
+// samples of ray r), samples 0 .. count[r] - 1 of each ray; otherwise count[r] is given
+// (the composite's live counts) and the samples first .. first + count[r] - 1 are taken.
+// sel_off: [n_rays + 1] (sel_off[n_rays] = the pass's total), tile_sums: scan scratch,
+// sel: the selected sample indices; evaluated accumulates the totals.
+void launch_render_select(uint32_t n_rays, const uint32_t* offsets, uint32_t* count, bool first_pass,
+                          uint32_t first, uint32_t* sel_off, uint32_t* tile_sums, uint32_t* sel,
+                          unsigned long long* evaluated, cudaStream_t s);
+// k_composite.cu: pass 1 (first kRenderFirst samples, live counts out) or pass 2 (the
+// live rays, from their first sample).
+void launch_composite_split(const DevCfg& c, uint32_t n_rays, int pass, uint32_t* live, const StepBufs& b,
+                            cudaStream_t s);
 
 // ---------------------------------------------------------------- grouped render
 // One piece of a grouped render (several views of several scenes in shared
@@ -160,7 +181,14 @@ void launch_field_fwd_fp32(const DevCfg& c, const float* params, uint32_t n_rays
 void launch_field_bwd_fp32(const DevCfg& c, const float* params, float* grads, uint32_t n_rays,
                            const StepBufs& b, int n_sm, cudaStream_t s, bool pose = false);
 
+// The forward over a selection of the batch's samples, sel[0 .. *n_sel) (a render's
+// passes; the encodings are not stored).
+void launch_field_fwd_fp32_sel(const DevCfg& c, const float* params, const uint32_t* sel, const uint32_t* n_sel,
+                               const StepBufs& b, int n_sm, cudaStream_t s);
+
 // k_field_tc.cu (FP16 / BF16 tensor-core MLP)
+void launch_field_fwd_tc_sel(const DevCfg& c, const float* params, const uint32_t* sel, const uint32_t* n_sel,
+                             const StepBufs& b, bool bf16, int n_sm, cudaStream_t s);
 void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b,
                          bool store_feat, bool bf16, int n_sm, cudaStream_t s);
 void launch_field_bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t n_rays,
@@ -173,7 +201,8 @@ void launch_pose_reduce(const DevCfg& c, uint32_t n_rays, const StepBufs& b, flo
 // k_composite.cu
 void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const StepBufs& b,
                       cudaStream_t s);
-void launch_write_render(const StepBufs& b, uint32_t n, float* rgb, float* depth, float* acc,
+// single_pass: the render evaluated every retained sample (counted as evaluated here).
+void launch_write_render(const StepBufs& b, uint32_t n, float* rgb, float* depth, float* acc, bool single_pass,
                          cudaStream_t s);
 
 // k_adam_occ.cu

@@ -61,13 +61,22 @@ __device__ __forceinline__ float warp_suffix(float x, uint32_t lane) {
 // the two passes and then (dL/dsigma_i, dL/dc_i).
 // kGroup (render only): the rays of a grouped render, each taking its sample spacing
 // and termination threshold from its piece (items[ray's kKf plane]).
-template <bool kBackward, bool kGroup = false>
+// kSplit (render only) composites in two passes around the forward's two passes:
+// 1 takes the first kRenderFirst samples of each ray and writes, per ray, the number of
+// samples still to evaluate into `live` (0 when the ray stopped at the threshold or
+// has no more samples); 2 takes the rays with live > 0 from their first sample to
+// their last.  A ray is composited in 32-sample chunks from its first sample in
+// every pass, so each result equals the single pass's.
+static_assert(kRenderFirst % 32 == 0, "the first pass must end at a chunk boundary of the compositing");
+
+template <bool kBackward, bool kGroup = false, int kSplit = 0>
 __global__ void __launch_bounds__(kCompositeWarps * 32) k_composite(
     DevCfg c, uint32_t n_rays, const float* __restrict__ rays, uint32_t cap, const uint32_t* __restrict__ offsets,
     const float* __restrict__ ts, const float4* __restrict__ sig_rgb, float4* __restrict__ scratch,
     float* __restrict__ ray_out, float* __restrict__ loss, float* __restrict__ partials,
-    const GroupItem* __restrict__ items = nullptr) {
+    const GroupItem* __restrict__ items = nullptr, uint32_t* __restrict__ live = nullptr) {
     static_assert(!(kBackward && kGroup), "grouped compositing is forward only");
+    static_assert(!(kBackward && kSplit), "two-pass compositing is forward only");
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const uint32_t n_warps = gridDim.x * kCompositeWarps;
     float delta = c.step_t, t_min = c.t_min;
@@ -80,9 +89,12 @@ __global__ void __launch_bounds__(kCompositeWarps * 32) k_composite(
             delta = it.c.step_t;
             t_min = it.c.t_min;
         }
-        const uint32_t a = offsets[r], b = offsets[r + 1];
+        if (kSplit == 2 && live[r] == 0) continue;  // warp-uniform
+        const uint32_t a = offsets[r], b_all = offsets[r + 1];
+        const uint32_t b = kSplit == 1 ? min(b_all, a + kRenderFirst) : b_all;
         float carry = 0.f;  // sum of sigma delta over the earlier chunks
         float Ir = 0.f, Ig = 0.f, Ib = 0.f, Dh = 0.f, acc = 0.f;
+        bool stopped = false;
         for (uint32_t base = a; base < b; base += 32) {
             const uint32_t s = base + lane;
             const bool in = s < b;
@@ -103,8 +115,12 @@ __global__ void __launch_bounds__(kCompositeWarps * 32) k_composite(
             acc += w;
             if (kBackward && in) scratch[s] = make_float4(w, expf(-(carry + incl)), 0.f, 0.f);
             carry += __shfl_sync(kFull, incl, 31);
-            if (!kBackward && __any_sync(kFull, in && T < t_min)) break;
+            if (!kBackward && __any_sync(kFull, in && T < t_min)) {
+                stopped = true;
+                break;
+            }
         }
+        if (kSplit == 1 && lane == 0) live[r] = stopped ? 0u : b_all - b;
         Ir = warp_sum(Ir);
         Ig = warp_sum(Ig);
         Ib = warp_sum(Ib);
@@ -228,6 +244,19 @@ void launch_composite_group(const GroupItem* items, uint32_t n_rays, const StepB
         unused, n_rays, b.rays, b.cap_rays, b.offsets, b.t, b.sig_rgb, nullptr, b.ray_out, nullptr, nullptr, items);
 }
 
+void launch_composite_split(const DevCfg& c, uint32_t n_rays, int pass, uint32_t* live, const StepBufs& b,
+                            cudaStream_t s) {
+    const uint32_t grid = composite_grid(n_rays);
+    if (pass == 1)
+        k_composite<false, false, 1><<<grid, kCompositeWarps * 32, 0, s>>>(
+            c, n_rays, b.rays, b.cap_rays, b.offsets, b.t, b.sig_rgb, nullptr, b.ray_out, nullptr, nullptr, nullptr,
+            live);
+    else
+        k_composite<false, false, 2><<<grid, kCompositeWarps * 32, 0, s>>>(
+            c, n_rays, b.rays, b.cap_rays, b.offsets, b.t, b.sig_rgb, nullptr, b.ray_out, nullptr, nullptr, nullptr,
+            live);
+}
+
 void launch_composite(const DevCfg& c, uint32_t n_rays, bool backward, const StepBufs& b,
                       cudaStream_t s) {
     const uint32_t grid = composite_grid(n_rays);
@@ -252,9 +281,13 @@ namespace nm {
 __global__ void k_write_render(const float* __restrict__ ray_out, uint32_t cap, uint32_t n,
                                float* __restrict__ rgb, float* __restrict__ depth,
                                float* __restrict__ acc, const uint32_t* __restrict__ chunk_total,
-                               unsigned long long* __restrict__ render_samples) {
+                               unsigned long long* __restrict__ render_samples,
+                               unsigned long long* __restrict__ evaluated) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r == 0) atomicAdd(render_samples, (unsigned long long)*chunk_total);
+    if (r == 0) {
+        atomicAdd(render_samples, (unsigned long long)*chunk_total);
+        if (evaluated) atomicAdd(evaluated, (unsigned long long)*chunk_total);  // single pass: all of them
+    }
     if (r >= n) return;
     if (rgb) {
         rgb[3 * r] = ray_out[r];
@@ -284,10 +317,11 @@ void launch_write_group(const GroupItem* items, uint32_t n_rays, const StepBufs&
     k_write_group<<<(n_rays + 255) / 256, 256, 0, s>>>(items, b.rays, b.ray_out, b.cap_rays, n_rays);
 }
 
-void launch_write_render(const StepBufs& b, uint32_t n, float* rgb, float* depth, float* acc,
+void launch_write_render(const StepBufs& b, uint32_t n, float* rgb, float* depth, float* acc, bool single_pass,
                          cudaStream_t s) {
     k_write_render<<<(n + 255) / 256, 256, 0, s>>>(b.ray_out, b.cap_rays, n, rgb, depth, acc, b.offsets + n,
-                                                   render_sample_counter(b));
+                                                   render_sample_counter(b),
+                                                   single_pass ? render_eval_counter(b) : nullptr);
 }
 
 }  // namespace nm

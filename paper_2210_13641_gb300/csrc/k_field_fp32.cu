@@ -83,13 +83,17 @@ __device__ __forceinline__ float3 color_mlp(const SmemW& s, const float* x3) {
     return make_float3(sigmoidf_(z0), sigmoidf_(z1), sigmoidf_(z2));
 }
 
+// kSel: the samples sel[0 .. *n_total) of the batch instead of 0 .. *n_total (a
+// render's passes); the encodings are not stored then.
+template <bool kSel>
 __global__ void __launch_bounds__(128) k_field_fwd_fp32(DevCfg c, const float* __restrict__ params,
                                                         const float* __restrict__ rays, uint32_t cap,
                                                         const uint32_t* __restrict__ n_total,
                                                         const uint32_t* __restrict__ ray_id,
                                                         const float* __restrict__ ts,
                                                         float4* __restrict__ sig_rgb,
-                                                        float* __restrict__ feat_out) {
+                                                        float* __restrict__ feat_out,
+                                                        const uint32_t* __restrict__ sel) {
     extern __shared__ float smem_raw[];
     SmemW& s = *reinterpret_cast<SmemW*>(smem_raw);
     const float* mlp = params + (size_t)c.L * c.T * 2;
@@ -97,13 +101,14 @@ __global__ void __launch_bounds__(128) k_field_fwd_fp32(DevCfg c, const float* _
     __syncthreads();
     const uint32_t n = *n_total;
     const float2* tables = reinterpret_cast<const float2*>(params);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const uint32_t i = kSel ? sel[j] : j;
         const uint32_t r = ray_id[i];
         float3 d;
         const float3 x = sample_pos(c, rays, cap, r, ts[i], d);
         float f[kEnc];
         hash_encode(c, tables, x, f);
-        if (feat_out) {
+        if (!kSel && feat_out) {
             float4* fo = reinterpret_cast<float4*>(feat_out + (size_t)i * kEnc);
 #pragma unroll
             for (int k = 0; k < kEnc / 4; ++k) fo[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
@@ -121,10 +126,19 @@ void launch_field_fwd_fp32(const DevCfg& c, const float* params, uint32_t n_rays
                            bool store_feat, int n_sm, cudaStream_t st) {
     const size_t smem = sizeof(SmemW);
     // per call: the attribute belongs to the current device (cheap next to the kernel)
-    cudaFuncSetAttribute(k_field_fwd_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_field_fwd_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     (void)n_rays;
-    k_field_fwd_fp32<<<n_sm * 8, 128, smem, st>>>(c, params, b.rays, b.cap_rays, b.offsets + n_rays,
-                                                 b.ray_id, b.t, b.sig_rgb, store_feat ? b.feat : nullptr);
+    k_field_fwd_fp32<false><<<n_sm * 8, 128, smem, st>>>(c, params, b.rays, b.cap_rays, b.offsets + n_rays,
+                                                        b.ray_id, b.t, b.sig_rgb, store_feat ? b.feat : nullptr,
+                                                        nullptr);
+}
+
+void launch_field_fwd_fp32_sel(const DevCfg& c, const float* params, const uint32_t* sel, const uint32_t* n_sel,
+                               const StepBufs& b, int n_sm, cudaStream_t st) {
+    const size_t smem = sizeof(SmemW);
+    cudaFuncSetAttribute(k_field_fwd_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_field_fwd_fp32<true><<<n_sm * 8, 128, smem, st>>>(c, params, b.rays, b.cap_rays, n_sel, b.ray_id, b.t,
+                                                       b.sig_rgb, nullptr, sel);
 }
 
 // ------------------------------------------------------------------ backward

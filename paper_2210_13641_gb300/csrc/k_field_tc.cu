@@ -199,13 +199,16 @@ constexpr int kFwdSmem = kWB + kT32 + kT64;                            // 45056
 // block owns sample row r.  smem: the weight tiles, then tA (128 x 32: X0, X3) and
 // tB (128 x 64: H1, H3, H4; a layer's MMAs have completed before its output
 // overwrites its input).  Returns after the tile's last MMA wait.
-template <bool BF16>
+// kSel: row r evaluates sample sel[i0 + r] of the batch instead of i0 + r (a render's
+// passes over a subset of the samples).
+template <bool BF16, bool kSel = false>
 __device__ __forceinline__ void fwd_tile(const DevCfg& c, const float2* __restrict__ tables,
                                          const float* __restrict__ rays, uint32_t cap,
                                          const uint32_t* __restrict__ ray_id, const float* __restrict__ ts,
                                          float4* __restrict__ sig_rgb, uint4* __restrict__ feat_out,
                                          float feat_scale, uint32_t i0, uint32_t i_end, uint8_t* smem,
-                                         uint32_t tmem, uint64_t* bar, uint32_t& phase, bool& timed_out) {
+                                         uint32_t tmem, uint64_t* bar, uint32_t& phase, bool& timed_out,
+                                         const uint32_t* __restrict__ sel = nullptr) {
     uint8_t* sW1 = smem;
     uint8_t* sW2 = sW1 + kW1B;
     uint8_t* sW3 = sW2 + kW2B;
@@ -216,8 +219,8 @@ __device__ __forceinline__ void fwd_tile(const DevCfg& c, const float2* __restri
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     const float inv_fs = 1.f / feat_scale;
-    const uint32_t i = i0 + tid;
-    const bool valid = i < i_end;
+    const bool valid = i0 + tid < i_end;
+    const uint32_t i = kSel ? (valid ? sel[i0 + tid] : 0u) : i0 + tid;
     float v[32];
     float3 d = make_float3(0.f, 0.f, 0.f);
     float3 x = make_float3(0.f, 0.f, 0.f);
@@ -239,7 +242,7 @@ __device__ __forceinline__ void fwd_tile(const DevCfg& c, const float2* __restri
         q.z = pack2<BF16>(v[4], v[5]);
         q.w = pack2<BF16>(v[6], v[7]);
         *reinterpret_cast<uint4*>(tA + tile_offset(tid, 8 * g, 128)) = q;
-        if (feat_out && valid) feat_out[(size_t)i * 4 + g] = q;
+        if (!kSel && feat_out && valid) feat_out[(size_t)i * 4 + g] = q;
     }
     // layer 1: D = X0 W1^T (128 x 64)
     to_tensor();
@@ -332,14 +335,15 @@ __device__ __forceinline__ void fwd_block_finish(uint32_t tmem, uint64_t* drain_
     if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, 64);
 }
 
-template <bool BF16>
+template <bool BF16, bool kSel = false>
 __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* __restrict__ params,
                                                       const float* __restrict__ rays, uint32_t cap,
                                                       const uint32_t* __restrict__ n_total,
                                                       const uint32_t* __restrict__ ray_id,
                                                       const float* __restrict__ ts, float4* __restrict__ sig_rgb,
                                                       uint4* __restrict__ feat_out, float feat_scale,
-                                                      uint32_t* __restrict__ err) {
+                                                      uint32_t* __restrict__ err,
+                                                      const uint32_t* __restrict__ sel = nullptr) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar, drain_bar;
     __shared__ uint32_t tslot;
@@ -353,8 +357,8 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
     bool timed_out = false;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t i0 = tile * 128;
-        fwd_tile<BF16>(c, tables, rays, cap, ray_id, ts, sig_rgb, feat_out, feat_scale, i0, n, smem, tmem, &bar, phase,
-                       timed_out);
+        fwd_tile<BF16, kSel>(c, tables, rays, cap, ray_id, ts, sig_rgb, feat_out, feat_scale, i0, n, smem, tmem, &bar,
+                             phase, timed_out, sel);
         fence_before_sync();
         if (__syncthreads_or(timed_out)) {
             if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
@@ -802,6 +806,21 @@ static void bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t 
     k_field_bwd_tc<BF16, kPose><<<n_sm * 2, 256, kBwdSmem, s>>>(
         c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays, b.ray_id, b.t, reinterpret_cast<const uint4*>(b.feat),
         b.sig_rgb, b.dsig_rgb, fs, b.loss, kPose ? b.pose_s : nullptr, b.err);
+}
+
+template <bool BF16>
+static void fwd_tc_sel(const DevCfg& c, const float* params, const uint32_t* sel, const uint32_t* n_sel,
+                       const StepBufs& b, int n_sm, cudaStream_t s) {
+    cudaFuncSetAttribute(k_field_fwd_tc<BF16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+    const float fs = BF16 ? 1.f : 256.f;
+    k_field_fwd_tc<BF16, true><<<n_sm * 4, 128, kFwdSmem, s>>>(c, params, b.rays, b.cap_rays, n_sel, b.ray_id, b.t,
+                                                                b.sig_rgb, nullptr, fs, b.err, sel);
+}
+
+void launch_field_fwd_tc_sel(const DevCfg& c, const float* params, const uint32_t* sel, const uint32_t* n_sel,
+                             const StepBufs& b, bool bf16, int n_sm, cudaStream_t s) {
+    if (bf16) fwd_tc_sel<true>(c, params, sel, n_sel, b, n_sm, s);
+    else fwd_tc_sel<false>(c, params, sel, n_sel, b, n_sm, s);
 }
 
 void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, const StepBufs& b, bool store_feat,

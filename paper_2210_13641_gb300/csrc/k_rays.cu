@@ -225,6 +225,37 @@ __global__ void k_scan_add(uint32_t* __restrict__ out, uint32_t n,
     if (i < n) out[i] += tile_sums[i / kScanTile];
 }
 
+// Selection of a render pass's samples: ray r contributes count[r] samples, its samples
+// k0 .. k0 + count[r] - 1 (counted from its first), at sel[sel_off[r] ...].
+__global__ void k_sel_emit(uint32_t n_rays, const uint32_t* __restrict__ offsets,
+                           const uint32_t* __restrict__ sel_off, const uint32_t* __restrict__ count, uint32_t k0,
+                           uint32_t* __restrict__ sel, unsigned long long* __restrict__ evaluated) {
+    const uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(evaluated, (unsigned long long)sel_off[n_rays]);
+    if (r >= n_rays) return;
+    const uint32_t n = count[r], dst = sel_off[r], src = offsets[r] + k0;
+    for (uint32_t k = lane; k < n; k += 32) sel[dst + k] = src + k;
+}
+
+// count[r] = min(first, samples of ray r): the first pass's share of each ray.
+__global__ void k_sel_first(uint32_t n_rays, const uint32_t* __restrict__ offsets, uint32_t first,
+                            uint32_t* __restrict__ count) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const uint32_t n = offsets[r + 1] - offsets[r];
+    count[r] = n < first ? n : first;
+}
+
+void launch_render_select(uint32_t n_rays, const uint32_t* offsets, uint32_t* count, bool first_pass,
+                          uint32_t first, uint32_t* sel_off, uint32_t* tile_sums, uint32_t* sel,
+                          unsigned long long* evaluated, cudaStream_t s) {
+    if (first_pass) k_sel_first<<<(n_rays + 255) / 256, 256, 0, s>>>(n_rays, offsets, first, count);
+    launch_scan_counts(count, n_rays, sel_off, tile_sums, s);
+    k_sel_emit<<<(n_rays + 7) / 8, 256, 0, s>>>(n_rays, offsets, sel_off, count, first_pass ? 0u : first, sel,
+                                                 evaluated);
+}
+
 void launch_compact(uint32_t n_rays, uint32_t row_stride, const uint32_t* offsets, const float* slots,
                     uint32_t* ray_id, float* ts, cudaStream_t s) {
     k_compact<<<(n_rays + 7) / 8, 256, 0, s>>>(n_rays, row_stride, offsets, slots, ray_id, ts);

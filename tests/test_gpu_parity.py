@@ -321,6 +321,36 @@ def test_render_in_chunks_matches_oracle_on_sampled_pixels():
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_two_pass_render_with_early_termination(prec):
+    """A dense field (most rays opaque within their first 32 samples) rendered with
+    the termination threshold: the render evaluates the field for the first 32
+    samples of each ray and then only for the rays still above the threshold
+    (map_stats.render_evaluated well below render_samples), and the image matches the
+    oracle's render with the same threshold (FP32 1e-5; FP16 2e-3 against the
+    oracle's FP16 rounding model), the rays that stop after their first 32 samples
+    included (the second pass evaluated more than the first pass's share)."""
+    cfg = synth.config_small(precision=prec, occ_res=0, step=np.float32(0.01), n_steps=300, max_samples=256)
+    P = synth.random_params(cfg, 31, table_scale=0.5, mlp_std=0.15)
+    P["W2"][0] += 2.6     # denser: about 3/4 of the rays stop within 32 samples, the rest later
+    m = _map(cfg, P, [synth.c1_keyframe(0, W=8, H=8)])
+    kf = synth.c1_keyframe(33, W=40, H=30)
+    rgb, D, acc = m.render(kf.c2w, kf.K, 40, 30)
+    st = m.stats()
+    o, d = oracle.render_rays_f32(np.asarray(kf.c2w, np.float32), np.asarray(kf.K, np.float32), 40, 30)
+    n_r = np.bincount(oracle.march(cfg, o, d)[0], minlength=40 * 30)
+    assert st.render_samples == n_r.sum() and n_r.mean() > 64
+    first = np.minimum(n_r, 32).sum()
+    assert first < st.render_evaluated < 0.7 * st.render_samples, (first, st.render_evaluated, st.render_samples)
+    I_ref, D_ref, A_ref = oracle.render(cfg, P, kf.c2w, kf.K, 40, 30, t_min=float(cfg.render_t_min), mlp_bits=prec)
+    tol = REL if prec == "fp32" else 2e-3
+    atol = 1e-6 if prec == "fp32" else 2e-3
+    assert np.allclose(rgb.reshape(-1, 3), I_ref, rtol=tol, atol=atol)
+    assert np.allclose(D.ravel(), D_ref, rtol=tol, atol=atol)
+    assert np.allclose(acc.ravel(), A_ref, rtol=tol, atol=atol)
+    m.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_maximum_samples_per_ray(prec):
     """The largest per-ray sample budget (max_samples = 1024): rays with hundreds of
     samples (many 32-sample chunks in the warp-per-ray march and compositing, many
