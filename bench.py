@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--no-forms", action="store_true", help="skip timing the other MLP precisions")
     p.add_argument("--no-serving", action="store_true", help="skip the multi-scene serving measurement")
     p.add_argument("--no-large-map", action="store_true", help="skip the large-map precision comparison")
+    p.add_argument("--no-fitted-render", action="store_true", help="skip the render of a map fitted further")
     p.add_argument("--large-map-keyframes", type=int, default=2000)
     p.add_argument("--large-map-rays", type=int, default=1 << 20)
     p.add_argument("--large-map-precisions", default="bf16,fp16,fp32")
@@ -865,12 +866,14 @@ def main():
 
     # ---------------- render of a fitted map: 300 more mapping steps make the surfaces
     # opaque, so rays stop early and the render evaluates fewer samples (two-pass render)
-    fit_steps = 300
-    for i in range(fit_steps):
-        m.step(n, seed=5000 + i, want_loss=False, stream=stream)
-    torch.cuda.synchronize()
-    render_fitted = time_renders()
-    render_fitted["fitted_steps"] = args.warmup + 2 * args.steps + fit_steps
+    render_fitted = None
+    if not args.no_fitted_render:
+        fit_steps = 300
+        for i in range(fit_steps):
+            m.step(n, seed=5000 + i, want_loss=False, stream=stream)
+        torch.cuda.synchronize()
+        render_fitted = time_renders()
+        render_fitted["fitted_steps"] = args.warmup + 2 * args.steps + fit_steps
 
     # ---------------- the other MLP precisions on the same workload (FP32 plain form, BF16)
     m.close()
