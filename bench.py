@@ -546,21 +546,21 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # FP16 tensor-core field kernels on this workload (2^18 rays, 15,869,619 samples),
-# from one ncu capture of the second timed step of `python bench.py --steps 2 --warmup 1
-# --no-cpu-baseline --no-forms --no-serving --no-large-map` with those metrics (one
+# from one ncu capture of the first timed step of `python bench.py --steps 2 --warmup 1
+# --no-cpu-baseline --no-forms --no-serving --no-large-map --no-fitted-render` with those metrics (one
 # pass), and the tensor pipe's and the L2's activity from one launch of the 32768-ray
 # case of the same command.  Valid only while the kernel sources are the ones captured:
 # the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
-    "sha256": "9bc920bae7ae00575f90446673242bf4e8e7636fb603899305c6078c6d4a55cb",
+    "sha256": "957079a4a115108111b2739a5fb61923f3fbf1e427eed94c11cf5a87e5e8fc09",
     "samples": 15869619,
-    "field_fwd": 295702016 + 1240706048,
-    "field_bwd": 1719796736 + 207590144,
+    "field_fwd": 295243776 + 1240113664,
+    "field_bwd": 1719678208 + 208460288,
     # sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed and
     # lts__throughput.avg.pct_of_peak_sustained_elapsed of one launch on the 32768-ray case
-    "tensor_pipe": {"field_fwd": 0.0373, "field_bwd": 0.0815},
-    "lts_throughput": {"field_fwd": 0.3272, "field_bwd": 0.5479},
+    "tensor_pipe": {"field_fwd": 0.0377, "field_bwd": 0.0813},
+    "lts_throughput": {"field_fwd": 0.3304, "field_bwd": 0.5459},
 }
 
 
