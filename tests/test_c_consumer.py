@@ -1,7 +1,8 @@
 """The boundary as a plain C program sees it (no GPU needed): include/nerfmap.h
 compiles as pedantic C99, a C program links against the in-tree libnerfmap.so, and
 the struct layout the C compiler gives map_config is the one the library was built
-with; an invalid configuration is refused with MAP_EINVAL and a message."""
+with; an invalid configuration is refused with MAP_EINVAL and a message; and
+map_config_init gives a C caller the level table the oracle computes."""
 
 import os
 import shutil
@@ -25,6 +26,11 @@ int main(void) {
     rc = map_create(&c, 0, &h);
     printf("%d %d\n", rc, h == NULL);
     printf("%s\n", map_last_error(NULL));
+    /* the library's level table for the room workload's grid (16 levels, 16..2048) */
+    rc = map_config_init(&c, 16, 19, 16, 2048, 0.0);
+    printf("%d", rc);
+    for (rc = 0; rc < 16; ++rc) printf(" %u", c.level_res[rc]);
+    printf("\n%u %u %u %.6g\n", c.n_features, c.enc_width, c.precision, (double)c.lr);
     return 0;
 }
 """
@@ -65,3 +71,9 @@ def test_c_program_links_and_agrees_on_the_layout(libdir, tmp_path):
     rc, null_handle = map(int, lines[1].split())
     assert rc == -1 and null_handle == 1        # MAP_EINVAL, no handle
     assert lines[2].strip()                      # a message
+    import oracle
+    import synth
+    res = list(map(int, lines[3].split()))
+    assert res[0] == 0 and res[1:] == oracle.level_resolutions(synth.config_c2())
+    f, e, prec, lr = lines[4].split()
+    assert (int(f), int(e), int(prec), float(lr)) == (2, 32, 1, 0.01)

@@ -160,6 +160,32 @@ def test_grouped_renders_equal_single_view_renders(prec):
         assert np.array_equal(rgb, single[(j, W, H)][0]) and np.array_equal(d, single[(j, W, H)][1])
 
 
+def test_render_group_refuses_plain_fp32_maps_and_bad_sizes():
+    """map_render_group takes tensor-core maps only (a plain FP32 map renders with
+    map_render) and refuses empty views, with MAP_EINVAL and a message on maps[0],
+    before anything is launched."""
+    import torch
+    from paper_2210_13641_gb300 import MapError, NerfMap, pack_params
+    from paper_2210_13641_gb300.binding import MAP_EINVAL, render_group
+    c16, c32 = synth.config_c1(precision="fp16"), synth.config_c1(precision="fp32")
+    m16, m32 = NerfMap(c16, occ_every=0), NerfMap(c32, occ_every=0)
+    m16.set_params(pack_params(synth.random_params(c16, 1)))
+    view = synth.c1_keyframe(52)
+    out = (torch.zeros((12, 16, 3), device="cuda"), torch.zeros((12, 16), device="cuda"))
+    with pytest.raises(MapError) as e:
+        render_group([m16, m32], [(view.c2w, view.K, 16, 12)] * 2, [out, out])
+    assert e.value.code == MAP_EINVAL and "FP32" in str(e.value)
+    with pytest.raises(MapError) as e:
+        render_group([m16], [(view.c2w, view.K, 0, 12)], [out])
+    assert e.value.code == MAP_EINVAL
+    render_group([m16], [(view.c2w, view.K, 16, 12)], [out])      # the valid call still works
+    torch.cuda.synchronize()
+    rgb0, d0, _ = m16.render(view.c2w, view.K, 16, 12)
+    assert np.array_equal(out[0].cpu().numpy(), rgb0) and np.array_equal(out[1].cpu().numpy(), d0)
+    m16.close()
+    m32.close()
+
+
 def test_keyframe_completes_after_a_covering_step_and_admission():
     from paper_2210_13641_gb300 import MapError, pack_params
     from paper_2210_13641_gb300.binding import MapServer
