@@ -239,8 +239,10 @@ int map_render(map_handle h, const float c2w[12], const float K[4], uint32_t W, 
  * launches (ray casting, march with each map's box and occupancy bitfield,
  * compaction, a persistent tensor-core field forward over 128-sample tiles that
  * never mix two views, switching weights where the map changes, compositing with
- * each map's render_t_min, output).  Every pixel goes through the arithmetic of
- * map_render of its view, and the images equal map_render's bit for bit.  Every map
+ * each map's render_t_min, output); as in map_render, with a threshold the field is
+ * evaluated for the first 32 samples of every ray and then only for the rays still
+ * above it.  Every pixel goes through the arithmetic of map_render of its view, and
+ * the images equal map_render's bit for bit.  Every map
  * must use the FP16 or BF16 MLP (plain FP32 maps: map_render).  All work is queued
  * on `stream`; the caller orders it after any work that changes the maps.  Work
  * buffers are held by maps[0] (allocated on first use).  Errors: MAP_EINVAL

@@ -114,6 +114,8 @@ struct GroupBufs {
     uint32_t row_stride = 0;
     GroupItem* items = nullptr;     // [kGroupMaxItems], device
     uint32_t* n_tiles = nullptr;    // [1], device
+    uint32_t* sel = nullptr;        // [cap_samples] a render pass's selected samples
+    uint32_t* sel_off = nullptr;    // [cap_rays + 1] its scan
 };
 
 // A scene's state as a grouped render needs it (api.cu).
@@ -146,11 +148,14 @@ int render_group(const GroupView* views, uint32_t n, bool bf16, GroupBufs& g, in
 
 // k_field_tc.cu: the grouped forward (persistent; switches weights where the scene
 // changes between tiles).
+// sel (nullable): the pieces' sample runs index this selection (a render pass).
 void launch_group_fwd_tc(const GroupItem* items, uint32_t n_items, const uint32_t* n_tiles, const StepBufs& b,
-                         bool bf16, int n_sm, cudaStream_t s);
+                         bool bf16, int n_sm, cudaStream_t s, const uint32_t* sel = nullptr);
 // k_composite.cu: the grouped render's compositing (each ray's spacing and
-// termination threshold from its piece) and output write.
-void launch_composite_group(const GroupItem* items, uint32_t n_rays, const StepBufs& b, cudaStream_t s);
+// termination threshold from its piece; pass 0: single pass, 1 / 2: the two render
+// passes with the live counts) and output write.
+void launch_composite_group(const GroupItem* items, uint32_t n_rays, const StepBufs& b, cudaStream_t s,
+                            int pass = 0, uint32_t* live = nullptr);
 void launch_write_group(const GroupItem* items, uint32_t n_rays, const StepBufs& b, cudaStream_t s);
 
 // k_rays.cu

@@ -238,10 +238,21 @@ static uint32_t composite_grid(uint32_t n_rays) {
     return grid;
 }
 
-void launch_composite_group(const GroupItem* items, uint32_t n_rays, const StepBufs& b, cudaStream_t s) {
+void launch_composite_group(const GroupItem* items, uint32_t n_rays, const StepBufs& b, cudaStream_t s, int pass,
+                            uint32_t* live) {
     DevCfg unused{};
-    k_composite<false, true><<<composite_grid(n_rays), kCompositeWarps * 32, 0, s>>>(
-        unused, n_rays, b.rays, b.cap_rays, b.offsets, b.t, b.sig_rgb, nullptr, b.ray_out, nullptr, nullptr, items);
+    const uint32_t grid = composite_grid(n_rays);
+    if (pass == 0)
+        k_composite<false, true><<<grid, kCompositeWarps * 32, 0, s>>>(
+            unused, n_rays, b.rays, b.cap_rays, b.offsets, b.t, b.sig_rgb, nullptr, b.ray_out, nullptr, nullptr, items);
+    else if (pass == 1)
+        k_composite<false, true, 1><<<grid, kCompositeWarps * 32, 0, s>>>(
+            unused, n_rays, b.rays, b.cap_rays, b.offsets, b.t, b.sig_rgb, nullptr, b.ray_out, nullptr, nullptr, items,
+            live);
+    else
+        k_composite<false, true, 2><<<grid, kCompositeWarps * 32, 0, s>>>(
+            unused, n_rays, b.rays, b.cap_rays, b.offsets, b.t, b.sig_rgb, nullptr, b.ray_out, nullptr, nullptr, items,
+            live);
 }
 
 void launch_composite_split(const DevCfg& c, uint32_t n_rays, int pass, uint32_t* live, const StepBufs& b,

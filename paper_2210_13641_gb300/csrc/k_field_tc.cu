@@ -374,13 +374,15 @@ __global__ void __launch_bounds__(128, 4) k_field_fwd_tc(DevCfg c, const float* 
 // block's previous one, the block copies that piece's configuration into shared
 // memory and, if the scene differs, rounds that scene's weights into the operand
 // tiles.  Each tile is then exactly the single-view forward's tile.
-template <bool BF16>
+// kSel: the pieces' runs s0 .. s0 + n_s - 1 index the selection sel (a render pass).
+template <bool BF16, bool kSel = false>
 __global__ void __launch_bounds__(128, 4) k_group_fwd_tc(const GroupItem* __restrict__ items, uint32_t n_items,
                                                       const uint32_t* __restrict__ n_tiles_total,
                                                       const float* __restrict__ rays, uint32_t cap,
                                                       const uint32_t* __restrict__ ray_id,
                                                       const float* __restrict__ ts, float4* __restrict__ sig_rgb,
-                                                      float feat_scale, uint32_t* __restrict__ err) {
+                                                      float feat_scale, uint32_t* __restrict__ err,
+                                                      const uint32_t* __restrict__ sel = nullptr) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar, drain_bar;
     __shared__ uint32_t tslot;
@@ -413,8 +415,8 @@ __global__ void __launch_bounds__(128, 4) k_group_fwd_tc(const GroupItem* __rest
             to_tensor();      // the weights to the tensor core, the configuration to every thread
         }
         const uint32_t k = (tile - tile0_s[j]) * 128;
-        fwd_tile<BF16>(cfg_s, reinterpret_cast<const float2*>(it.params), rays, cap, ray_id, ts, sig_rgb, nullptr,
-                       feat_scale, it.s0 + k, it.s0 + it.n_s, smem, tmem, &bar, phase, timed_out);
+        fwd_tile<BF16, kSel>(cfg_s, reinterpret_cast<const float2*>(it.params), rays, cap, ray_id, ts, sig_rgb,
+                             nullptr, feat_scale, it.s0 + k, it.s0 + it.n_s, smem, tmem, &bar, phase, timed_out, sel);
         fence_before_sync();
         if (__syncthreads_or(timed_out)) {
             if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
@@ -829,17 +831,22 @@ void launch_field_fwd_tc(const DevCfg& c, const float* params, uint32_t n_rays, 
     else fwd_tc<false>(c, params, n_rays, b, store_feat, n_sm, s);
 }
 
+template <bool BF16, bool kSel>
+static void group_fwd(const GroupItem* items, uint32_t n_items, const uint32_t* n_tiles, const StepBufs& b,
+                      const uint32_t* sel, int n_sm, cudaStream_t s) {
+    cudaFuncSetAttribute(k_group_fwd_tc<BF16, kSel>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+    k_group_fwd_tc<BF16, kSel><<<n_sm * 4, 128, kFwdSmem, s>>>(items, n_items, n_tiles, b.rays, b.cap_rays, b.ray_id,
+                                                                b.t, b.sig_rgb, BF16 ? 1.f : 256.f, b.err, sel);
+}
+
 void launch_group_fwd_tc(const GroupItem* items, uint32_t n_items, const uint32_t* n_tiles, const StepBufs& b,
-                         bool bf16, int n_sm, cudaStream_t s) {
-    const float fs = bf16 ? 1.f : 256.f;
-    if (bf16) {
-        cudaFuncSetAttribute(k_group_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
-        k_group_fwd_tc<true><<<n_sm * 4, 128, kFwdSmem, s>>>(items, n_items, n_tiles, b.rays, b.cap_rays, b.ray_id,
-                                                              b.t, b.sig_rgb, fs, b.err);
+                         bool bf16, int n_sm, cudaStream_t s, const uint32_t* sel) {
+    if (sel) {
+        if (bf16) group_fwd<true, true>(items, n_items, n_tiles, b, sel, n_sm, s);
+        else group_fwd<false, true>(items, n_items, n_tiles, b, sel, n_sm, s);
     } else {
-        cudaFuncSetAttribute(k_group_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
-        k_group_fwd_tc<false><<<n_sm * 4, 128, kFwdSmem, s>>>(items, n_items, n_tiles, b.rays, b.cap_rays,
-                                                               b.ray_id, b.t, b.sig_rgb, fs, b.err);
+        if (bf16) group_fwd<true, false>(items, n_items, n_tiles, b, sel, n_sm, s);
+        else group_fwd<false, false>(items, n_items, n_tiles, b, sel, n_sm, s);
     }
 }
 

@@ -7,7 +7,9 @@
 // the tensor-core field forward, compositing and the output write - with each ray
 // taking its scene's configuration, parameters and bitfield from its piece.  The
 // field forward runs over 128-sample tiles that never mix two pieces, so every sample
-// goes through exactly the arithmetic of a render of its view alone, and the grouped
+// goes through exactly the arithmetic of a render of its view alone; like map_render,
+// the field is evaluated in two passes when a threshold is set (the first
+// kRenderFirst samples of every ray, then the rays still above it), and the grouped
 // result equals the single-view render bit for bit.
 #include <algorithm>
 
@@ -83,8 +85,9 @@ __global__ void k_group_march(const GroupItem* __restrict__ items, uint32_t n_ra
     if (lane == 0) counts[r] = n < max_samples ? n : max_samples;
 }
 
-// After the scan: each piece's samples (a contiguous run, the batch is ray-major) and
-// its tiles; the batch's tile count.
+// After a scan over the rays (the march's, or a render pass's selection): each
+// piece's run of samples (contiguous: the batch is ray-major) and its tiles; the
+// batch's tile count.
 __global__ void k_group_tiles(GroupItem* __restrict__ items, uint32_t n_items, const uint32_t* __restrict__ offsets,
                               uint32_t* __restrict__ n_tiles) {
     if (threadIdx.x != 0) return;
@@ -122,6 +125,9 @@ int group_bufs_alloc(GroupBufs& g, uint32_t cap_rays, uint32_t row_stride) {
         {(void**)&b.err, 64},
         {(void**)&g.items, sizeof(GroupItem) * kGroupMaxItems},
         {(void**)&g.n_tiles, 64},
+        {(void**)&g.sel, sizeof(uint32_t) * cs},
+        {(void**)&g.sel_off, sizeof(uint32_t) * (cap_rays + 1)},
+        {(void**)&b.loss, 64},
     };
     for (auto& r : reqs) {
         if (cudaMalloc(r.p, r.bytes) != cudaSuccess) {
@@ -132,6 +138,7 @@ int group_bufs_alloc(GroupBufs& g, uint32_t cap_rays, uint32_t row_stride) {
         }
     }
     cudaMemset(b.err, 0, 64);
+    cudaMemset(b.loss, 0, 64);
     b.cap_rays = cap_rays;
     b.cap_samples = cs;
     g.b = b;
@@ -141,7 +148,7 @@ int group_bufs_alloc(GroupBufs& g, uint32_t cap_rays, uint32_t row_stride) {
 
 void group_bufs_free(GroupBufs& g) {
     void* ps[] = {g.b.rays, g.b.counts, g.b.offsets, g.b.block_sums, g.b.ray_id, g.b.t, g.b.sig_rgb,
-                  g.b.ray_out, g.b.err, g.items, g.n_tiles};
+                  g.b.ray_out, g.b.err, g.items, g.n_tiles, g.sel, g.sel_off, g.b.loss};
     for (void* p : ps)
         if (p) cudaFree(p);
     g = GroupBufs{};
@@ -154,6 +161,8 @@ int render_group(const GroupView* views, uint32_t n, bool bf16, GroupBufs& g, in
         if (views[v].scene.dc.max_samples > g.row_stride || views[v].scene.precision == MAP_PREC_FP32 ||
             (views[v].scene.precision == MAP_PREC_BF16) != bf16)
             return MAP_EINVAL;
+    bool two_pass = false;  // early termination saves field work when a view has a threshold
+    for (uint32_t k = 0; k < n; ++k) two_pass |= views[k].scene.dc.t_min > 0.f;
     uint32_t v = 0, p = 0;  // next view and its next pixel
     while (v < n) {
         GroupItems its{};
@@ -188,12 +197,25 @@ int render_group(const GroupView* views, uint32_t n, bool bf16, GroupBufs& g, in
                                                      g.row_stride);
         launch_scan_counts(b.counts, rays, b.offsets, b.block_sums, s);
         launch_compact(rays, g.row_stride, b.offsets, slots, b.ray_id, b.t, s);
-        k_group_tiles<<<1, 32, 0, s>>>(g.items, n_items, b.offsets, g.n_tiles);
-        launch_group_fwd_tc(g.items, n_items, g.n_tiles, b, bf16, n_sm, s);
-        launch_composite_group(g.items, rays, b, s);
+        if (!two_pass) {
+            k_group_tiles<<<1, 32, 0, s>>>(g.items, n_items, b.offsets, g.n_tiles);
+            launch_group_fwd_tc(g.items, n_items, g.n_tiles, b, bf16, n_sm, s);
+            launch_composite_group(g.items, rays, b, s);
+            if (launches) *launches += 11;  // items, rays, march, 3 scan passes, compaction, tiles, field, composite, write
+        } else {
+            // as map_render: the field for the first kRenderFirst samples of every ray,
+            // then for the rays still above their threshold (pieces index the selection)
+            for (int pass = 1; pass <= 2; ++pass) {
+                launch_render_select(rays, b.offsets, b.counts, pass == 1, kRenderFirst, g.sel_off, b.block_sums,
+                                     g.sel, render_eval_counter(b), s);
+                k_group_tiles<<<1, 32, 0, s>>>(g.items, n_items, g.sel_off, g.n_tiles);
+                launch_group_fwd_tc(g.items, n_items, g.n_tiles, b, bf16, n_sm, s, g.sel);
+                launch_composite_group(g.items, rays, b, s, pass, b.counts);
+            }
+            if (launches) *launches += 23;
+        }
         launch_write_group(g.items, rays, b, s);
         if (cudaGetLastError() != cudaSuccess) return MAP_ECUDA;
-        if (launches) *launches += 11;  // items, rays, march, 3 scan passes, compaction, tiles, field, composite, write
     }
     return MAP_OK;
 }

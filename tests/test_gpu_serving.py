@@ -103,19 +103,23 @@ def test_results_same_alone_and_in_the_mix(prec):
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_grouped_renders_equal_single_view_renders(prec):
-    """Nine views of three maps (different table sizes, grids, bitfields and weights)
-    at 160x120, 640x480 and 1280x720 in one map_render_group call (batches of 2^18
-    rays that mix views, scenes and resolutions, views split across batches): every
-    image equals, bit for bit, the mapping library's own render of that view
-    (map_render, parity-tested against the oracle).  The same queries through the
-    serving loop go through grouped renders and give the same images."""
+    """Twelve views of four maps (different table sizes, grids, bitfields and
+    weights, one of them dense enough that most rays stop within their first 32
+    samples) at 160x120, 640x480 and 1280x720 in one map_render_group call (batches
+    of 2^18 rays that mix views, scenes and resolutions, views split across batches,
+    both render passes): every image equals, bit for bit, the mapping library's own
+    render of that view (map_render, parity-tested against the oracle).  The same
+    queries through the serving loop go through grouped renders and give the same
+    images."""
     import torch
     from paper_2210_13641_gb300 import NerfMap, pack_params
     from paper_2210_13641_gb300.binding import MapServer, render_group
     cfgs = [synth.config_c1(precision=prec),
             synth.config_small(precision=prec, occ_res=16, step=np.float32(0.02), n_steps=150),
-            synth.config_small(precision=prec, occ_res=0, log2_table=12)]
+            synth.config_small(precision=prec, occ_res=0, log2_table=12),
+            synth.config_small(precision=prec, occ_res=0, step=np.float32(0.01), n_steps=300, max_samples=256)]
     Ps = [synth.random_params(c, 20 + j, table_scale=0.5, mlp_std=0.15) for j, c in enumerate(cfgs)]
+    Ps[3]["W2"][0] += 2.6      # a dense field: most rays stop early, the passes matter
     bits = np.packbits(np.random.default_rng(5).uniform(size=16 ** 3) < 0.6, bitorder="little")
     view = synth.c1_keyframe(51)
     sizes = ((160, 120), (640, 480), (1280, 720))
@@ -126,7 +130,7 @@ def test_grouped_renders_equal_single_view_renders(prec):
         if c.occ_res:
             m.set_occupancy(bits)
         maps.append(m)
-    order = [(j, W, H) for W, H in sizes for j in range(3)]          # resolutions and scenes interleaved
+    order = [(j, W, H) for W, H in sizes for j in range(len(cfgs))]  # resolutions and scenes interleaved
     outs = [(torch.full((H, W, 3), -1.0, device="cuda"), torch.full((H, W), -1.0, device="cuda"))
             for _, W, H in order]
     render_group([maps[j] for j, _, _ in order], [(view.c2w, _scaled(view, W, H), W, H) for _, W, H in order],
