@@ -553,14 +553,14 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 # the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
-    "sha256": "957079a4a115108111b2739a5fb61923f3fbf1e427eed94c11cf5a87e5e8fc09",
+    "sha256": "dfe5795667063e154d9b181e64b5991893c8415af3e66a4145dcf7008cb19acf",
     "samples": 15869619,
-    "field_fwd": 295243776 + 1240113664,
-    "field_bwd": 1719678208 + 208460288,
+    "field_fwd": 295538432 + 1240316416,
+    "field_bwd": 1719958016 + 208148992,
     # sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed and
     # lts__throughput.avg.pct_of_peak_sustained_elapsed of one launch on the 32768-ray case
-    "tensor_pipe": {"field_fwd": 0.0377, "field_bwd": 0.0813},
-    "lts_throughput": {"field_fwd": 0.3304, "field_bwd": 0.5459},
+    "tensor_pipe": {"field_fwd": 0.0376, "field_bwd": 0.0815},
+    "lts_throughput": {"field_fwd": 0.3296, "field_bwd": 0.5467},
 }
 
 
