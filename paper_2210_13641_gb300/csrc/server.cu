@@ -312,6 +312,14 @@ bool issue_group(map_server_s* s) {
                 r->grouped = true;
             }
         }
+        if (L.stream) {
+            // the scenes' later steps wait for the grouped render (whatever of it was
+            // queued, also when a launch failed part way: it still reads the parameters)
+            cudaEvent_t done = s->get_event();
+            cudaEventRecord(done, L.stream);
+            for (Scene* sc : scenes) cudaStreamWaitEvent(sc->stream, done, 0);
+            s->event_pool.push_back(done);
+        }
         if (rc != MAP_OK) {
             for (auto& br : batch) {
                 s->release_pin(br.second);
@@ -325,10 +333,6 @@ bool issue_group(map_server_s* s) {
             cudaEventRecord(r->ev, L.stream);
             br.first->inflight.push_back(r);
         }
-        cudaEvent_t done = s->get_event();
-        cudaEventRecord(done, L.stream);
-        for (Scene* sc : scenes) cudaStreamWaitEvent(sc->stream, done, 0);  // later steps wait for the render
-        s->event_pool.push_back(done);
         s->grouped_renders += batch.size();
         s->group_batches += 1;
     }
