@@ -457,7 +457,8 @@ def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0, group_renders=T
     continuous mapping (2^16-ray steps), each receiving a 640x480 keyframe at 10 Hz,
     plus render queries (160x120, 640x480, 1280x720) arriving as a Poisson stream of
     30 per second over random scenes.  Returns p50/p99 latencies and the aggregate
-    mapping rays/s of the window."""
+    mapping rays/s of the window; then the latency of 20 bursts of one 160x120
+    render query per scene, all four submitted at once."""
     import numpy as np
     import synth
     from paper_2210_13641_gb300 import pack_params
@@ -509,6 +510,19 @@ def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0, group_renders=T
     done = server.wait(list(ids), timeout=600)
     elapsed = time.perf_counter() - t0
     st1 = server.stats()
+    # bursts: one small render query to every scene at the same moment (a viewer of
+    # all four maps), 20 rounds; each round's latency is until its last image is done
+    burst = []
+    v = kfs[0]
+    Wb, Hb = 160, 120
+    Kb = np.array([v.K[0] * Wb / v.W, v.K[1] * Hb / v.H, Wb / 2.0, Hb / 2.0], np.float32)
+    for _ in range(20):
+        tb = time.perf_counter()
+        rids = [server.submit_render(sid, v.c2w, Kb, Wb, Hb)[0] for sid in scenes]
+        server.wait(rids, timeout=120)
+        burst.append(time.perf_counter() - tb)
+        time.sleep(0.02)
+    st2 = server.stats()
     server.close()
     lat = {}
     for rid, (kind, tag) in ids.items():
@@ -525,6 +539,9 @@ def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0, group_renders=T
     for k, v in lat.items():
         out[f"{k}_ms_p50"] = pct(v, 50)
         out[f"{k}_ms_p99"] = pct(v, 99)
+    out["burst_4x160x120_ms_p50"] = pct(burst, 50)
+    out["burst_4x160x120_ms_p99"] = pct(burst, 99)
+    out["burst_group_batches"] = st2["group_batches"] - st1["group_batches"]
     return out
 
 
