@@ -452,9 +452,11 @@ def large_map_benchmark(n_kf=2000, W=1200, H=680, rays=1 << 20, steps=5, warmup=
 
 # ----------------------------------------------------------------- serving
 
-def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0, group_renders=True):
+def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0, group_renders=True, step_rays=1 << 16,
+                      max_inflight=1):
     """Four resident scenes (tables 2^16 .. 2^19 per level, the room workload) with
-    continuous mapping (2^16-ray steps), each receiving a 640x480 keyframe at 10 Hz,
+    continuous mapping (step_rays-ray steps, max_inflight requests per scene on the
+    GPU at a time), each receiving a 640x480 keyframe at 10 Hz,
     plus render queries (160x120, 640x480, 1280x720) arriving as a Poisson stream of
     30 per second over random scenes.  Returns p50/p99 latencies and the aggregate
     mapping rays/s of the window; then the latency of 20 bursts of one 160x120
@@ -464,7 +466,7 @@ def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0, group_renders=T
     from paper_2210_13641_gb300 import pack_params
     from paper_2210_13641_gb300.binding import MapServer
     rng = np.random.default_rng(seed)
-    server = MapServer(max_scenes=4, max_inflight=2, step_rays=1 << 16, group_renders=group_renders)
+    server = MapServer(max_scenes=4, max_inflight=max_inflight, step_rays=step_rays, group_renders=group_renders)
     scenes = []
     for j, log2t in enumerate((16, 17, 18, 19)):
         cfg = synth.config_c2(precision=precision, log2_table=log2t, seed=j)
@@ -532,6 +534,7 @@ def serving_benchmark(precision, kfs, bits, seconds=6.0, seed=0, group_renders=T
             lat.setdefault("render_" + tag, []).append(d["t_done"] - d["t_submit"])
     pct = lambda v, q: float(np.percentile(np.array(v) * 1e3, q))
     out = {"precision": precision, "window_s": round(elapsed, 2), "group_renders": bool(group_renders),
+           "step_rays": step_rays, "max_inflight": max_inflight,
            "mapping_rays_per_s": (st1["rays_done"] - st0["rays_done"]) / elapsed,
            "requests": {k: len(v) for k, v in lat.items()},
            "grouped_renders": st1["grouped_renders"] - st0["grouped_renders"],
@@ -928,6 +931,9 @@ def main():
         if args.precision != "fp32":
             serving[args.precision + "_ungrouped"] = serving_benchmark(args.precision, kfs, bits, args.serving_seconds,
                                                                        group_renders=False)
+            # shorter mapping steps: a keyframe waits behind less work, for a few % of throughput
+            serving[args.precision + "_steps_32768"] = serving_benchmark(args.precision, kfs, bits,
+                                                                         args.serving_seconds, step_rays=1 << 15)
     large = None
     if not args.no_large_map and rank == 0:
         large = large_map_benchmark(n_kf=args.large_map_keyframes, rays=args.large_map_rays,

@@ -456,9 +456,12 @@ class NerfMap:
 
 
 class MapServer:
-    """Multi-scene serving loop (map_server_* of the C ABI)."""
+    """Multi-scene serving loop (map_server_* of the C ABI).  One request per scene on
+    the GPU at a time by default: with several scenes the device stays busy with the
+    others' work, and a new keyframe or render waits behind one mapping step of its
+    scene instead of two."""
 
-    def __init__(self, max_scenes=4, max_inflight=2, step_rays=1 << 18, hbm_reserve=1 << 30,
+    def __init__(self, max_scenes=4, max_inflight=1, step_rays=1 << 18, hbm_reserve=1 << 30,
                  kf_reserve=1 << 30, seed=0, group_renders=True):
         self.lib = load()
         c = ServerConfig(max_scenes, max_inflight, step_rays, int(group_renders), hbm_reserve, kf_reserve, seed)
