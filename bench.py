@@ -573,14 +573,14 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 # the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
-    "sha256": "dfe5795667063e154d9b181e64b5991893c8415af3e66a4145dcf7008cb19acf",
+    "sha256": "b3e82b99a51636e936cbce62bb294a620e21f2b95358a1e2b43b98129ac79fbe",
     "samples": 15869619,
-    "field_fwd": 295538432 + 1240316416,
-    "field_bwd": 1719958016 + 208148992,
+    "field_fwd": 295460864 + 1239959296,
+    "field_bwd": 1718229504 + 149891584,
     # sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed and
     # lts__throughput.avg.pct_of_peak_sustained_elapsed of one launch on the 32768-ray case
-    "tensor_pipe": {"field_fwd": 0.0376, "field_bwd": 0.0815},
-    "lts_throughput": {"field_fwd": 0.3296, "field_bwd": 0.5467},
+    "tensor_pipe": {"field_fwd": 0.0378, "field_bwd": 0.0870},
+    "lts_throughput": {"field_fwd": 0.3308, "field_bwd": 0.5799},
 }
 
 

@@ -91,9 +91,10 @@ __device__ __forceinline__ void hash_encode(const DevCfg& c, const float2* __res
     for (int l0 = 0; l0 < kEnc / 2; l0 += kGatherGroup) encode_group(c, tables, x, l0, f + 2 * l0);
 }
 
-// dL/dtable[l][slot_k] += w_k * dL/df_l for every corner and level (FP32 vector
-// reductions of 8 bytes, one per corner), warp-cooperative: called by all 32 lanes
-// (lanes with valid = false contribute nothing).  Consecutive samples of a ray fall into the
+// dL/dtable[l][slot_k] += w_k * dL/df_l for every corner and for the levels whose
+// bit is set in `levels` (FP32 vector reductions of 8 bytes, one per corner),
+// warp-cooperative: called by all 32 lanes (lanes with valid = false contribute
+// nothing).  df(l) returns this lane's (dL/df_{l,0}, dL/df_{l,1}) as a float2.  Consecutive samples of a ray fall into the
 // same cell of the coarse levels, so per level the lanes with equal cells (runs of
 // consecutive lanes) first sum their 8 corner contributions with a segmented
 // shuffle reduction, and only the first lane of each run issues the 8 atomics.
@@ -109,14 +110,15 @@ __device__ __forceinline__ void hash_encode(const DevCfg& c, const float2* __res
 // rounds: every extra head costs 8 reductions, which the large map's HBM-resident
 // tables pay dearly (cutting runs every 8 lanes: -1 % on a 64 MB table, +20 % on a
 // 512 MB one).
-template <bool kButterfly>
+template <bool kButterfly, class DF>
 __device__ __forceinline__ void hash_scatter_warp(const DevCfg& c, float2* __restrict__ gtables,
-                                                  float3 x, const float* df, bool valid) {
+                                                  float3 x, DF df, bool valid, uint32_t levels = 0xFFFFu) {
     const uint32_t Tmask = c.T - 1;
     const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll 2
     for (int l = 0; l < kEnc / 2; ++l) {
         if (l >= (int)c.L) break;
+        if (!((levels >> l) & 1u)) continue;
         const uint32_t N = c.res[l];
         const bool dense = (c.dense_mask >> l) & 1u;
         uint32_t cx, cy, cz;
@@ -125,7 +127,8 @@ __device__ __forceinline__ void hash_scatter_warp(const DevCfg& c, float2* __res
         level_cell(x.y, N, cy, wy);
         level_cell(x.z, N, cz, wz);
         float2* gtab = gtables + (size_t)l * c.T;
-        const float g0 = valid ? df[2 * l] : 0.f, g1 = valid ? df[2 * l + 1] : 0.f;
+        const float2 gl = df(l);
+        const float g0 = valid ? gl.x : 0.f, g1 = valid ? gl.y : 0.f;
         const uint64_t key = valid ? (((uint64_t)cz << 42) | ((uint64_t)cy << 21) | cx) : ~(uint64_t)lane;
         const uint64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
         const bool head = lane == 0 || prev != key;

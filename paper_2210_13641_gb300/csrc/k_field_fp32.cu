@@ -381,7 +381,8 @@ __global__ void __launch_bounds__(kTile) k_field_bwd_fp32(DevCfg c, const float*
                     for (int k = 0; k < kEnc; ++k) df[k] += W1[j * kEnc + k] * a;
                 }
             }
-            hash_scatter_warp<false>(c, gtables, x, df, valid);
+            hash_scatter_warp<false>(c, gtables, x, [&](int l) { return make_float2(df[2 * l], df[2 * l + 1]); },
+                                     valid);
             if (kPose && valid) {
                 const float3 gx = hash_grad_x(c, reinterpret_cast<const float2*>(params), x, df);
                 pose_s[2 * (size_t)i] = make_float4(gx.x * c.inv_size, gx.y * c.inv_size, gx.z * c.inv_size, 0.f);

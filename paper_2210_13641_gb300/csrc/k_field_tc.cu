@@ -427,25 +427,38 @@ __global__ void __launch_bounds__(128, 4) k_group_fwd_tc(const GroupItem* __rest
 }
 
 // ------------------------------------------------------------------ backward
-// Warp-specialised: warps 0-3 (the "MLP" group, thread r = sample row r = TMEM
-// lane r) run the layer chain on the tensor cores; warps 4-7 (the "IO" group,
-// thread 128 + r serves row r) load each tile's inputs one tile ahead and scatter
-// each finished tile's encoding gradient into the tables while the MLP group
-// works on the next tile.  The groups hand tiles over through named barriers:
-//   kBarIn      IO -> MLP  the tile's encodings (X0) and row data are in place
-//   kBarDfReady MLP -> IO  the chain is done (X0 free) and dL/dfeat is in smem
-//   kBarDfFree  IO -> MLP  the dL/dfeat buffer has been read
-// Both groups walk the same tile list and meet every barrier, whatever happens
-// to an MMA wait (a timed-out wait only skips waiting), so no barrier can block.
+// Warp-specialised in three warpgroups: warps 0-3 (the "MLP" group, thread r =
+// sample row r = TMEM lane r) run the layer chain on the tensor cores; warps 4-7
+// (the "IO" group, thread 128 + r serves row r) load each tile's inputs one tile
+// ahead and scatter the even levels of each finished tile's encoding gradient into
+// the tables; warps 8-11 (the "SC" group, thread 256 + r) scatter its odd levels.
+// Both scatter groups work on tile k while the MLP group runs tile k + 1: the
+// scatter is the longer path (its reductions and warp shuffles load the L1 data
+// pipe), so it gets two warpgroups.  Registers are split with setmaxnreg: the
+// block is launched with 80 per thread (two blocks of 384 threads per SM), the
+// MLP group takes 128, the IO group 64 (its prefetched inputs are dead while it
+// scatters), the SC group 48: 128 x 128 + 128 x 64 + 128 x 48 = 384 x 80.  The
+// groups hand tiles over through named barriers:
+//   kBarIn      IO -> MLP        the tile's encodings (X0) and row data are in place
+//   kBarDfReady MLP -> IO, SC    the chain is done (X0 free) and dL/dfeat is in smem
+//   kBarDfFree  IO, SC -> MLP    both scatters of the tile are done (dL/dfeat read)
+// All groups walk the same tile list and meet every barrier, whatever happens to
+// an MMA wait (a timed-out wait only skips waiting), so no barrier can block.
 //
 // TMEM columns: [0,64) layer chain, [64,128) dW4, [128,160) dW3, [160,192) dW1,
 // [192,208) dW2^T, [208,224) dW5^T.  The weight gradients are M=64 products: row m
 // of such an accumulator is TMEM lane 32*(m/16) + m%16.
 constexpr uint32_t kColW4 = 64, kColW3 = 128, kColW1 = 160, kColW2T = 192, kColW5T = 208;
 constexpr int kBarMlp = 1, kBarIn = 2, kBarDfReady = 3, kBarDfFree = 4;
-constexpr int kDfBytes = 128 * 32 * 4;      // dL/dfeat rows, 16-byte chunks xor-swizzled by row
+constexpr int kBwdThreads = 384;            // MLP, IO and SC warpgroups
+constexpr uint32_t kRegMlp = 128, kRegIo = 64, kRegSc = 48;
+static_assert(128 * (kRegMlp + kRegIo + kRegSc) == kBwdThreads * 80,
+              "the setmaxnreg split must add up to the launch allocation (80 registers per thread)");
+constexpr uint32_t kLevelsIo = 0x5555u, kLevelsSc = 0xAAAAu;  // even / odd levels
+constexpr int kDfBytes = 128 * 32 * 4;      // dL/dfeat, [level][row] float2
 constexpr int kRowBytes = 128 * 32;         // row data: {d.xyz, valid}, {dz0, dz1, dz2, dL/dsigma}
-constexpr int kBwdSmem = kWB + kT32 + kT64 + kT32 + kT64 + kT64 + kT16 + kDfBytes + kRowBytes;  // 110592
+constexpr int kXBytes = 2 * 128 * 16;       // sample positions (x, valid) of the tiles, by parity
+constexpr int kBwdSmem = kWB + kT32 + kT64 + kT32 + kT64 + kT64 + kT16 + kDfBytes + kRowBytes + kXBytes;  // 114688
 
 namespace {
 
@@ -499,7 +512,6 @@ __device__ __forceinline__ void mask_epilogue(uint32_t trow, uint8_t* tile, int 
     }
 }
 
-__device__ __forceinline__ uint32_t df_offset(int r, int q) { return (uint32_t)(r * 128 + ((q ^ (r & 7)) << 4)); }
 
 }  // namespace
 
@@ -507,7 +519,7 @@ __device__ __forceinline__ uint32_t df_offset(int r, int q) { return (uint32_t)(
 // view-direction gradient through the SH encoding (MLP group) into pose_s[2 i],
 // pose_s[2 i + 1].
 template <bool BF16, bool kPose>
-__global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* __restrict__ params,
+__global__ void __launch_bounds__(kBwdThreads, 2) k_field_bwd_tc(DevCfg c, const float* __restrict__ params,
                                                          float* __restrict__ grads, const float* __restrict__ rays,
                                                          uint32_t cap, const uint32_t* __restrict__ n_total,
                                                          const uint32_t* __restrict__ ray_id,
@@ -532,6 +544,8 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
     uint8_t* tG5 = tH4 + kT64;   // 128 x 16
     uint8_t* sDf = tG5 + kT16;   // 128 rows x 32 FP32
     float4* sRow = reinterpret_cast<float4*>(sDf + kDfBytes);  // [128][2]
+    float4* sX = sRow + 2 * 128;                                // [2][128]: (x, valid) of tile k at k & 1
+    const float2* sDf2 = reinterpret_cast<const float2*>(sDf);
 
     const int tid = threadIdx.x, warp = tid >> 5, r = tid & 127;
     load_weight_tiles<BF16>(params + (size_t)c.L * c.T * 2, sW1, sW2, sW3, sW4, sW5);
@@ -555,6 +569,7 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
     bool timed_out = false;
 
     if (warp < 4) {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kRegMlp));
         // ======================= MLP group: the layer chain on the tensor cores
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         const float inv_fs = 1.f / feat_scale;
@@ -672,15 +687,14 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
             wait_mma(&bar, phase, timed_out, c.wait_polls);
             ld_cols<32>(trow, 0, v);
             fence_before_sync();
-            if (k > 0) nb_sync(kBarDfFree, 256);          // the IO group has read the previous tile's rows
+            if (k > 0) nb_sync(kBarDfFree, kBwdThreads);  // both scatters of the previous tile are done
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                *reinterpret_cast<float4*>(sDf + df_offset(r, q)) =
-                    make_float4(v[4 * q] * inv_S, v[4 * q + 1] * inv_S, v[4 * q + 2] * inv_S, v[4 * q + 3] * inv_S);
-            nb_arrive(kBarDfReady, 256);                  // also: X0 and the row data are free
+            for (int q = 0; q < 16; ++q)
+                reinterpret_cast<float2*>(sDf)[q * 128 + r] = make_float2(v[2 * q] * inv_S, v[2 * q + 1] * inv_S);
+            nb_arrive(kBarDfReady, kBwdThreads);          // also: X0 and the row data are free
         }
         // ---- flush the weight gradients (lane 32*(m/16) + m%16 holds row m)
-        const bool any_timeout = __syncthreads_or(timed_out) != 0;  // both groups take part
+        const bool any_timeout = __syncthreads_or(timed_out) != 0;  // all three groups take part
         fence_after_sync();
         if (any_timeout && r == 0) drain_mma(&drain_bar);          // r == 0 issued every MMA
         if (n_mine > 0 && !any_timeout) {
@@ -709,8 +723,21 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                 for (int q = 0; q < 3; ++q) atomicAdd(gm_ + kOffW5 + q * 64 + m, w[q] * inv_Sc);
         }
         if (any_timeout && tid == 0) atomicOr(err, kErrTimeout);
+    } else if (warp >= 8) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kRegSc));
+        // ======================= SC group: the odd levels' gradient scatter
+        float2* gtables = reinterpret_cast<float2*>(grads);
+        for (uint32_t k = 0; k < n_mine; ++k) {
+            nb_sync(kBarDfReady, kBwdThreads);
+            const float4 xq = sX[(k & 1u) * 128 + r];
+            hash_scatter_warp<true>(c, gtables, make_float3(xq.x, xq.y, xq.z),
+                                    [&](int l) { return sDf2[l * 128 + r]; }, xq.w != 0.f, kLevelsSc);
+            if (k + 1 < n_mine) nb_arrive(kBarDfFree, kBwdThreads);
+        }
+        __syncthreads_or(false);                      // pairs with the MLP group's flush barrier
     } else {
-        // ======================= IO group: tile inputs one tile ahead, gradient scatter
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kRegIo));
+        // ======================= IO group: tile inputs one tile ahead, the even levels' scatter
         float2* gtables = reinterpret_cast<float2*>(grads);
         float3 x_cur = make_float3(0.f, 0.f, 0.f), x_next = x_cur;
         bool valid_cur = false, valid_next = false;
@@ -738,7 +765,10 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
                                       Sc * g.w * col.w * (1.f - col.w), g.x);
             }
         };
-        auto publish = [&]() {
+        // the inputs of tile kk into the operand tile and the row data (and its sample
+        // positions for the SC group)
+        auto publish = [&](uint32_t kk) {
+            sX[(kk & 1u) * 128 + r] = make_float4(x_next.x, x_next.y, x_next.z, valid_next ? 1.f : 0.f);
 #pragma unroll
             for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(tX0 + tile_offset(r, 8 * q, 128)) = f_next[q];
             sRow[2 * r] = rd_next;
@@ -751,31 +781,30 @@ __global__ void __launch_bounds__(256, 2) k_field_bwd_tc(DevCfg c, const float* 
         };
         if (n_mine > 0) {
             load(0);
-            publish();
+            publish(0);
         }
         for (uint32_t k = 0; k < n_mine; ++k) {
             if (k + 1 < n_mine) load(k + 1);          // global loads in flight during the chain
-            nb_sync(kBarDfReady, 256);
+            nb_sync(kBarDfReady, kBwdThreads);
             const float3 x_done = x_cur;
             const bool valid_done = valid_cur;
             const uint32_t i_done = i_cur;
-            float v[32];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float4 a = *reinterpret_cast<const float4*>(sDf + df_offset(r, q));
-                v[4 * q] = a.x;
-                v[4 * q + 1] = a.y;
-                v[4 * q + 2] = a.z;
-                v[4 * q + 3] = a.w;
-            }
-            if (k + 1 < n_mine) publish();            // next tile's inputs; the MLP group starts on it
-            if (k + 1 < n_mine) nb_arrive(kBarDfFree, 256);
-            hash_scatter_warp<true>(c, gtables, x_done, v, valid_done);
+            if (k + 1 < n_mine) publish(k + 1);       // next tile's inputs; the MLP group starts on it
+            hash_scatter_warp<true>(c, gtables, x_done, [&](int l) { return sDf2[l * 128 + r]; }, valid_done,
+                                    kLevelsIo);
             if (kPose && valid_done) {
+                float v[32];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float2 a = sDf2[q * 128 + r];
+                    v[2 * q] = a.x;
+                    v[2 * q + 1] = a.y;
+                }
                 const float3 gx = hash_grad_x(c, reinterpret_cast<const float2*>(params), x_done, v);
                 pose_s[2 * (size_t)i_done] =
                     make_float4(gx.x * c.inv_size, gx.y * c.inv_size, gx.z * c.inv_size, 0.f);
             }
+            if (k + 1 < n_mine) nb_arrive(kBarDfFree, kBwdThreads);  // dL/dfeat read: the MLP group may overwrite it
         }
         __syncthreads_or(false);                      // pairs with the MLP group's flush barrier
     }
@@ -805,7 +834,7 @@ static void bwd_tc(const DevCfg& c, const float* params, float* grads, uint32_t 
     // per call: the attribute belongs to the current device (cheap next to the kernel)
     cudaFuncSetAttribute(k_field_bwd_tc<BF16, kPose>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem);
     const float fs = BF16 ? 1.f : 256.f;
-    k_field_bwd_tc<BF16, kPose><<<n_sm * 2, 256, kBwdSmem, s>>>(
+    k_field_bwd_tc<BF16, kPose><<<n_sm * 2, kBwdThreads, kBwdSmem, s>>>(
         c, params, grads, b.rays, b.cap_rays, b.offsets + n_rays, b.ray_id, b.t, reinterpret_cast<const uint4*>(b.feat),
         b.sig_rgb, b.dsig_rgb, fs, b.loss, kPose ? b.pose_s : nullptr, b.err);
 }
