@@ -436,8 +436,9 @@ __global__ void __launch_bounds__(128, 4) k_group_fwd_tc(const GroupItem* __rest
 // scatter is the longer path (its reductions and warp shuffles load the L1 data
 // pipe), so it gets two warpgroups.  Registers are split with setmaxnreg: the
 // block is launched with 80 per thread (two blocks of 384 threads per SM), the
-// MLP group takes 128, the IO group 64 (its prefetched inputs are dead while it
-// scatters), the SC group 48: 128 x 128 + 128 x 64 + 128 x 48 = 384 x 80.  The
+// MLP group takes 136, the IO group 64 (its prefetched inputs are dead while it
+// scatters), the SC group 40 (the scatter alone needs no more without spilling):
+// 128 x 136 + 128 x 64 + 128 x 40 = 384 x 80.  The
 // groups hand tiles over through named barriers:
 //   kBarIn      IO -> MLP        the tile's encodings (X0) and row data are in place
 //   kBarDfReady MLP -> IO, SC    the chain is done (X0 free) and dL/dfeat is in smem
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(128, 4) k_group_fwd_tc(const GroupItem* __rest
 constexpr uint32_t kColW4 = 64, kColW3 = 128, kColW1 = 160, kColW2T = 192, kColW5T = 208;
 constexpr int kBarMlp = 1, kBarIn = 2, kBarDfReady = 3, kBarDfFree = 4;
 constexpr int kBwdThreads = 384;            // MLP, IO and SC warpgroups
-constexpr uint32_t kRegMlp = 128, kRegIo = 64, kRegSc = 48;
+constexpr uint32_t kRegMlp = 136, kRegIo = 64, kRegSc = 40;
 static_assert(128 * (kRegMlp + kRegIo + kRegSc) == kBwdThreads * 80,
               "the setmaxnreg split must add up to the launch allocation (80 registers per thread)");
 constexpr uint32_t kLevelsIo = 0x5555u, kLevelsSc = 0xAAAAu;  // even / odd levels
