@@ -573,14 +573,14 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 # the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
-    "sha256": "b3e82b99a51636e936cbce62bb294a620e21f2b95358a1e2b43b98129ac79fbe",
+    "sha256": "2fdcfa9e252232e4e7a46e485cf6318b40485bb6948810ec216a95fe66d97b24",
     "samples": 15869619,
-    "field_fwd": 295460864 + 1239959296,
-    "field_bwd": 1718229504 + 149891584,
+    "field_fwd": 296292352 + 1241936896,
+    "field_bwd": 1719506688 + 98251008,
     # sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed and
     # lts__throughput.avg.pct_of_peak_sustained_elapsed of one launch on the 32768-ray case
-    "tensor_pipe": {"field_fwd": 0.0378, "field_bwd": 0.0870},
-    "lts_throughput": {"field_fwd": 0.3308, "field_bwd": 0.5799},
+    "tensor_pipe": {"field_fwd": 0.0395, "field_bwd": 0.0874},
+    "lts_throughput": {"field_fwd": 0.3192, "field_bwd": 0.5789},
 }
 
 
