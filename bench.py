@@ -581,6 +581,10 @@ NCU_TRAFFIC = {
     # lts__throughput.avg.pct_of_peak_sustained_elapsed of one launch on the 32768-ray case
     "tensor_pipe": {"field_fwd": 0.0395, "field_bwd": 0.0874},
     "lts_throughput": {"field_fwd": 0.3192, "field_bwd": 0.5789},
+    # l1tex__data_pipe_lsu_wavefronts.sum.pct_of_peak_sustained_elapsed of the same launches: the
+    # pipe that carries the gathers' and reductions' per-lane traffic, the shuffles and the
+    # shared-memory operand stores (the field kernels' binding unit at this workload)
+    "l1_data_pipe": {"field_fwd": 0.7273, "field_bwd": 0.6682},
 }
 
 
@@ -638,10 +642,12 @@ def roofline(cfg, prof, n_samples, n_params, precision):
     for k, peak_key in (("field_fwd", "stream_read_gbs"), ("field_bwd", "stream_reduce_gbs")):
         ach = table_bytes / (cand[k] / 1e3) / 1e9
         tr = measured_traffic(k, precision, n_samples)
-        lts = (NCU_TRAFFIC["lts_throughput"][k] if precision == "fp16" and
-               kernel_sources_digest() == NCU_TRAFFIC["sha256"] else None)
+        cur = precision == "fp16" and kernel_sources_digest() == NCU_TRAFFIC["sha256"]
+        lts = NCU_TRAFFIC["lts_throughput"][k] if cur else None
+        l1 = NCU_TRAFFIC["l1_data_pipe"][k] if cur else None
         kernels[k] = {"bound": "l2", "achieved": ach, "peak": l2[peak_key], "unit": "GB/s",
                       "frac": ach / l2[peak_key], "ms": cand[k], "ncu_lts_throughput": lts,
+                      "ncu_l1_data_pipe": l1,
                       "frac_of_random_ceiling": ach / l2["random_read_gbs" if k == "field_fwd" else "random_reduce_gbs"],
                       "hbm": {"traffic": tr, "achieved": None if tr is None else tr / (cand[k] / 1e3) / 1e9,
                               "peak": hbm, "frac": None if tr is None else tr / (cand[k] / 1e3) / 1e9 / hbm}}
