@@ -263,16 +263,17 @@ def test_full_size_room_step_sampled(room_workload, prec):
 _ROOM_PLAIN = {}
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
 def test_full_size_room_backward(room_workload, prec):
     """The backward of the benchmark's workload (L=16, T=2^19, N up to 2048, the
     128^3 bitfield, 20 keyframes of 640x480) on 16384 rays, through the same
     launches as the benchmark's step: the field kernels' persistent grids are sized
     by the SM count, not by the batch, so the ~1M samples give every backward block
     about 26 tiles of 128 samples and every forward block about 13.  FP32: loss 1e-5,
-    every gradient tensor 1e-5 relative and element-wise against grads_abs.  FP16:
-    loss and every gradient tensor 2e-3 against the oracle's FP16 rounding model, and
-    2e-3 plus that model's distance from the plain oracle against the plain oracle."""
+    every gradient tensor 1e-5 relative and element-wise against grads_abs.  FP16 and
+    BF16: loss and every gradient tensor 2e-3 against the oracle's rounding model of
+    the format, and 2e-3 plus that model's distance from the plain oracle against the
+    plain oracle."""
     cfg, kfs, bits, P = room_workload
     cfg = cfg.replace(precision=prec)
     n, seed = 16384, 23
