@@ -423,7 +423,9 @@ typedef struct map_server_s* map_server;
 
 typedef struct map_server_config {
     uint32_t max_scenes;        /* scene slots, 1..64 */
-    uint32_t max_inflight;      /* requests per scene on the GPU at once (>= 1) */
+    uint32_t max_inflight;      /* requests per scene on the GPU at once (>= 1); with several scenes
+                                   1 gives the lowest keyframe and render latency at the same
+                                   mapping throughput (the other scenes keep the GPU busy) */
     uint32_t step_rays;         /* rays of a continuous-mapping step */
     uint32_t group_renders;     /* 1: render queries of the FP16 / BF16 scenes that are due together
                                    run as one grouped render (see below); 0: each on its own */
