@@ -310,6 +310,30 @@ int map_evict_keyframe(map_handle h, uint32_t kf_id, void* stream);
 int map_restore_keyframe(map_handle h, uint32_t kf_id, void* stream);
 int map_keyframe_resident(map_handle h, uint32_t kf_id);
 
+/*
+ * Checkpoint (the paper has none: a mapping run that is stopped and resumed later,
+ * or moved to another process).  map_save writes the map's state to the file `path`:
+ * its configuration, the parameters, the Adam moments and step count, the occupancy
+ * bitfield and density EMA, the occupancy refresh counter and, with
+ * MAP_SAVE_KEYFRAMES, every keyframe (id, pose, intrinsics, size, residency and its
+ * images in the map's own texel format, depth already in ray units).  The gradient
+ * buffer is not saved: it is zero after every step that updates the map.  It waits
+ * for the stream first.  Little-endian file, versioned; MAP_EINVAL (with a message)
+ * when the file cannot be written.
+ * map_load creates a map from such a file, as map_create would with the saved
+ * configuration and hbm_budget_bytes, and restores that state bit for bit: with the
+ * keyframes saved, its next map_step (same n_rays, seed and flags) draws the same
+ * rays and samples and returns the same loss as the saved map's next step would (the
+ * table gradients then agree up to the order of their FP32 atomics); without them it
+ * has no keyframes (map_step: MAP_ENOKF) until they are added again.
+ * Streamed-out keyframes are restored streamed out.  MAP_EINVAL for a missing,
+ * truncated or foreign file or a configuration this library does not accept;
+ * MAP_ENOMEM as map_create.
+ */
+#define MAP_SAVE_KEYFRAMES 1u
+int map_save(map_handle h, const char* path, uint32_t flags, void* stream);
+int map_load(const char* path, size_t hbm_budget_bytes, map_handle* out);
+
 /* The kf_id of each keyframe slot: ids[s] for s < min(n, number of keyframes);
  * returns the number of keyframes (host memory). */
 int map_get_keyframe_ids(map_handle h, uint32_t* ids, uint32_t n);

@@ -21,6 +21,7 @@ MAP_OK, MAP_EINVAL, MAP_ENOMEM, MAP_ENOKF, MAP_ETIMEOUT, MAP_ECUDA = 0, -1, -2, 
 MAP_MEM_HOST, MAP_MEM_DEVICE = 0, 1
 MAP_STEP_NO_UPDATE = 1
 MAP_STEP_POSE_GRAD = 2
+MAP_SAVE_KEYFRAMES = 1
 PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2}
 MLP_SHAPES = [("W1", (64, 32)), ("W2", (16, 64)), ("W3", (64, 32)), ("W4", (64, 64)), ("W5", (3, 64))]
 MLP_PARAMS = sum(a * b for _, (a, b) in MLP_SHAPES)
@@ -108,6 +109,8 @@ _SIGS = {
     "map_evict_keyframe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "map_restore_keyframe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "map_keyframe_resident": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "map_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "map_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
     "map_marginal_covariances": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -278,6 +281,28 @@ class NerfMap:
             raise MapError(rc, self.lib.map_last_error(None).decode())
         self.h = h
         self.n_params = self.stats().param_count
+
+    @classmethod
+    def load(cls, path, cfg, hbm_budget: int = 0) -> "NerfMap":
+        """The map saved in `path` by save() (map_load).  cfg: the field configuration it
+        was created with (used by the Python-side helpers such as unpack)."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        self.cfg = cfg
+        self.ccfg = None
+        h = ctypes.c_void_p()
+        rc = self.lib.map_load(os.fsencode(str(path)), hbm_budget, ctypes.byref(h))
+        if rc != MAP_OK:
+            raise MapError(rc, self.lib.map_last_error(None).decode())
+        self.h = h
+        self.n_params = self.stats().param_count
+        return self
+
+    def save(self, path, keyframes: bool = True, stream=None):
+        """Checkpoint of the map's state into `path` (map_save); with keyframes=True the
+        keyframe images too, so that a loaded map resumes bit for bit."""
+        self._check(self.lib.map_save(self.h, os.fsencode(str(path)), MAP_SAVE_KEYFRAMES if keyframes else 0,
+                                      _stream(stream)))
 
     def _check(self, rc):
         if rc != MAP_OK:

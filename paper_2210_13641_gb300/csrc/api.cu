@@ -672,6 +672,170 @@ int map_keyframe_resident(map_handle h, uint32_t kf_id) {
     return fail(h, MAP_EINVAL, "unknown kf_id");
 }
 
+// ------------------------------------------------------------------ checkpoint
+// File layout (host byte order; both supported hosts are little-endian):
+//   "NMAPCKPT", u32 version, u32 flags, u32 sizeof(map_config), map_config,
+//   u64 step, u64 n_refresh, u64 n_params, f32 params / adam_m / adam_v [n_params],
+//   u32 n_cells, u8 bits [n_cells / 8], f32 density [n_cells],
+//   u32 n_kf, per keyframe: u32 id, W, H, resident, f32 c2w[12], K[4], u64 bytes, texels.
+namespace {
+
+constexpr char kCkptMagic[8] = {'N', 'M', 'A', 'P', 'C', 'K', 'P', 'T'};
+constexpr uint32_t kCkptVersion = 1;
+constexpr size_t kCkptChunk = size_t(64) << 20;
+
+struct CkptFile {
+    FILE* f = nullptr;
+    ~CkptFile() {
+        if (f) std::fclose(f);
+    }
+};
+
+bool ck_write(FILE* f, const void* p, size_t n) { return std::fwrite(p, 1, n, f) == n; }
+bool ck_read(FILE* f, void* p, size_t n) { return std::fread(p, 1, n, f) == n; }
+
+// Device memory to the file (and back) through a host buffer, in chunks.
+bool ck_write_dev(FILE* f, const void* d, size_t n, std::vector<uint8_t>& tmp) {
+    for (size_t o = 0; o < n; o += kCkptChunk) {
+        const size_t m = std::min(kCkptChunk, n - o);
+        tmp.resize(m);
+        if (cudaMemcpy(tmp.data(), static_cast<const uint8_t*>(d) + o, m, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return false;
+        if (!ck_write(f, tmp.data(), m)) return false;
+    }
+    return true;
+}
+
+bool ck_read_dev(FILE* f, void* d, size_t n, std::vector<uint8_t>& tmp) {
+    for (size_t o = 0; o < n; o += kCkptChunk) {
+        const size_t m = std::min(kCkptChunk, n - o);
+        tmp.resize(m);
+        if (!ck_read(f, tmp.data(), m)) return false;
+        if (cudaMemcpy(static_cast<uint8_t*>(d) + o, tmp.data(), m, cudaMemcpyHostToDevice) != cudaSuccess)
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+int map_save(map_handle h, const char* path, uint32_t flags, void* stream) {
+    if (!h) return MAP_EINVAL;
+    if (!path) return fail(h, MAP_EINVAL, "null path");
+    if (flags & ~MAP_SAVE_KEYFRAMES) return fail(h, MAP_EINVAL, "unknown checkpoint flags");
+    NM_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
+    CkptFile F;
+    F.f = std::fopen(path, "wb");
+    if (!F.f) return fail(h, MAP_EINVAL, std::string("cannot open ") + path + " for writing");
+    std::vector<uint8_t> tmp;
+    const uint32_t cfg_size = sizeof(map_config);
+    const uint64_t step = h->step, n_refresh = h->n_refresh, n_params = h->n_params;
+    const uint32_t n_cells = h->n_cells;
+    const uint32_t n_kf = (flags & MAP_SAVE_KEYFRAMES) ? (uint32_t)h->kfs.size() : 0u;
+    const size_t pb = h->n_params * sizeof(float);
+    bool ok = ck_write(F.f, kCkptMagic, sizeof(kCkptMagic)) && ck_write(F.f, &kCkptVersion, 4) &&
+              ck_write(F.f, &flags, 4) && ck_write(F.f, &cfg_size, 4) && ck_write(F.f, &h->cfg, cfg_size) &&
+              ck_write(F.f, &step, 8) && ck_write(F.f, &n_refresh, 8) && ck_write(F.f, &n_params, 8) &&
+              ck_write_dev(F.f, h->params, pb, tmp) && ck_write_dev(F.f, h->adam_m, pb, tmp) &&
+              ck_write_dev(F.f, h->adam_v, pb, tmp) && ck_write(F.f, &n_cells, 4);
+    if (ok && n_cells)
+        ok = ck_write_dev(F.f, h->occ_bits, n_cells / 8, tmp) &&
+             ck_write_dev(F.f, h->occ_density, (size_t)n_cells * sizeof(float), tmp);
+    ok = ok && ck_write(F.f, &n_kf, 4);
+    for (uint32_t i = 0; ok && i < n_kf; ++i) {
+        const Keyframe& kf = h->kfs[i];
+        const KfDesc& d = h->kf_desc[i];
+        const uint32_t rec[4] = {kf.id, kf.W, kf.H, kf.texels ? 1u : 0u};
+        const uint64_t bytes = kf.bytes;
+        ok = ck_write(F.f, rec, sizeof(rec)) && ck_write(F.f, d.c2w, sizeof(d.c2w)) &&
+             ck_write(F.f, d.K, sizeof(d.K)) && ck_write(F.f, &bytes, 8) &&
+             (kf.texels ? ck_write_dev(F.f, kf.texels, kf.bytes, tmp) : ck_write(F.f, kf.host, kf.bytes));
+    }
+    const bool closed = std::fclose(F.f) == 0;
+    F.f = nullptr;
+    if (!ok || !closed) return fail(h, MAP_EINVAL, std::string("writing ") + path + " failed");
+    return MAP_OK;
+}
+
+int map_load(const char* path, size_t hbm_budget_bytes, map_handle* out) {
+    g_global_error.clear();
+    if (!out) return fail(nullptr, MAP_EINVAL, "null output handle");
+    *out = nullptr;
+    if (!path) return fail(nullptr, MAP_EINVAL, "null path");
+    CkptFile F;
+    F.f = std::fopen(path, "rb");
+    if (!F.f) return fail(nullptr, MAP_EINVAL, std::string("cannot open ") + path);
+    char magic[8];
+    uint32_t version = 0, flags = 0, cfg_size = 0;
+    map_config cfg;
+    if (!ck_read(F.f, magic, 8) || std::memcmp(magic, kCkptMagic, 8) != 0 || !ck_read(F.f, &version, 4) ||
+        version != kCkptVersion || !ck_read(F.f, &flags, 4) || !ck_read(F.f, &cfg_size, 4) ||
+        cfg_size != sizeof(map_config) || !ck_read(F.f, &cfg, sizeof(cfg)))
+        return fail(nullptr, MAP_EINVAL, std::string(path) + ": not a checkpoint of this library version");
+    uint64_t step = 0, n_refresh = 0, n_params = 0;
+    if (!ck_read(F.f, &step, 8) || !ck_read(F.f, &n_refresh, 8) || !ck_read(F.f, &n_params, 8))
+        return fail(nullptr, MAP_EINVAL, std::string(path) + ": truncated");
+    map_handle h = nullptr;
+    int rc = map_create(&cfg, hbm_budget_bytes, &h);
+    if (rc) return rc;
+    auto bad = [&](const std::string& what) {
+        map_destroy(h);
+        return fail(nullptr, MAP_EINVAL, std::string(path) + ": " + what);
+    };
+    if (n_params != h->n_params) return bad("parameter count does not match its configuration");
+    std::vector<uint8_t> tmp;
+    const size_t pb = h->n_params * sizeof(float);
+    if (!ck_read_dev(F.f, h->params, pb, tmp) || !ck_read_dev(F.f, h->adam_m, pb, tmp) ||
+        !ck_read_dev(F.f, h->adam_v, pb, tmp))
+        return bad("truncated parameters");
+    uint32_t n_cells = 0;
+    if (!ck_read(F.f, &n_cells, 4) || n_cells != h->n_cells) return bad("occupancy grid does not match");
+    if (n_cells && (!ck_read_dev(F.f, h->occ_bits, n_cells / 8, tmp) ||
+                    !ck_read_dev(F.f, h->occ_density, (size_t)n_cells * sizeof(float), tmp)))
+        return bad("truncated occupancy grid");
+    h->step = step;
+    h->n_refresh = n_refresh;
+    uint32_t n_kf = 0;
+    if (!ck_read(F.f, &n_kf, 4)) return bad("truncated keyframe table");
+    for (uint32_t i = 0; i < n_kf; ++i) {
+        uint32_t rec[4];
+        KfDesc d{};
+        uint64_t bytes = 0;
+        if (!ck_read(F.f, rec, sizeof(rec)) || !ck_read(F.f, d.c2w, sizeof(d.c2w)) ||
+            !ck_read(F.f, d.K, sizeof(d.K)) || !ck_read(F.f, &bytes, 8))
+            return bad("truncated keyframe table");
+        const uint32_t W = rec[1], H = rec[2];
+        if (W == 0 || H == 0 || (uint64_t)W * H > (1ull << 26) || bytes != (uint64_t)W * H * 2 * sizeof(float4))
+            return bad("bad keyframe record");
+        // the map owns each buffer as soon as it exists (map_destroy frees it on failure)
+        Keyframe kf{rec[0], W, H, nullptr, (size_t)bytes};
+        if (rec[3]) {
+            if (dalloc(h, (void**)&kf.texels, kf.bytes)) return bad("no device memory for the keyframes");
+            h->kfs.push_back(kf);
+            if (!ck_read_dev(F.f, kf.texels, kf.bytes, tmp)) return bad("truncated keyframe images");
+        } else {
+            if (cudaMallocHost((void**)&kf.host, kf.bytes) != cudaSuccess) return bad("no host memory");
+            h->kfs.push_back(kf);
+            if (!ck_read(F.f, kf.host, kf.bytes)) return bad("truncated keyframe images");
+        }
+        d.W = W;
+        d.H = H;
+        d.texels = kf.texels;
+        h->kf_desc.push_back(d);
+    }
+    if (n_kf) {
+        const uint32_t cap = std::max<uint32_t>(64, n_kf * 2);
+        if (dalloc(h, (void**)&h->d_kfs, cap * sizeof(KfDesc))) return bad("no device memory for the keyframes");
+        h->d_kfs_cap = cap;
+        for (uint32_t i = 0; i < n_kf; ++i) launch_set_kf_desc(h->d_kfs, i, h->kf_desc[i], nullptr);
+        if (rebuild_active(h, nullptr) != MAP_OK) return bad(h->err);
+    }
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return bad(std::string("restore: ") + cudaGetErrorString(e));
+    *out = h;
+    return MAP_OK;
+}
+
 int map_get_pose_grads(map_handle h, float* dst, uint32_t n_kf, int mem_kind, void* stream) {
     if (!h) return MAP_EINVAL;
     if (!dst || n_kf > h->kfs.size()) return fail(h, MAP_EINVAL, "n_kf exceeds the number of keyframes");

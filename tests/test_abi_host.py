@@ -66,6 +66,25 @@ def test_invalid_configs_rejected_before_device_use(lib):
         assert lib.map_last_error(None)
 
 
+def test_checkpoint_refusals_before_device_use(lib, tmp_path):
+    """map_load rejects a missing, foreign or truncated file (and map_save a null map)
+    with MAP_EINVAL and a message, before it touches a device."""
+    from paper_2210_13641_gb300 import binding
+    h = ctypes.c_void_p()
+    assert lib.map_load(str(tmp_path / "missing.ckpt").encode(), 0, ctypes.byref(h)) == binding.MAP_EINVAL
+    assert b"cannot open" in lib.map_last_error(None) and not h.value
+    foreign = tmp_path / "foreign.ckpt"
+    foreign.write_bytes(b"not a map checkpoint at all" * 4)
+    assert lib.map_load(str(foreign).encode(), 0, ctypes.byref(h)) == binding.MAP_EINVAL
+    assert b"not a checkpoint" in lib.map_last_error(None)
+    truncated = tmp_path / "truncated.ckpt"
+    truncated.write_bytes(b"NMAPCKPT" + (1).to_bytes(4, "little"))
+    assert lib.map_load(str(truncated).encode(), 0, ctypes.byref(h)) == binding.MAP_EINVAL
+    assert lib.map_load(None, 0, ctypes.byref(h)) == binding.MAP_EINVAL
+    assert lib.map_load(str(foreign).encode(), 0, None) == binding.MAP_EINVAL
+    assert lib.map_save(None, str(tmp_path / "x.ckpt").encode(), 1, None) == binding.MAP_EINVAL
+
+
 @pytest.mark.parametrize("mk", [synth.config_small, synth.config_c1, synth.config_c2, synth.config_c5])
 def test_level_table_matches_oracle(lib, mk):
     """The library's level table (map_config_init, host only) equals the oracle's."""
@@ -133,7 +152,7 @@ def test_binding_constants_match_the_header():
     from paper_2210_13641_gb300 import binding
     d = _header_defines()
     for name in ("MAP_OK", "MAP_EINVAL", "MAP_ENOMEM", "MAP_ENOKF", "MAP_ETIMEOUT", "MAP_ECUDA",
-                 "MAP_MEM_HOST", "MAP_MEM_DEVICE", "MAP_STEP_NO_UPDATE", "MAP_STEP_POSE_GRAD"):
+                 "MAP_MEM_HOST", "MAP_MEM_DEVICE", "MAP_STEP_NO_UPDATE", "MAP_STEP_POSE_GRAD", "MAP_SAVE_KEYFRAMES"):
         assert getattr(binding, name) == d[name], name
     assert binding.PRECISION == {"fp32": d["MAP_PREC_FP32"], "fp16": d["MAP_PREC_FP16"], "bf16": d["MAP_PREC_BF16"]}
     assert (binding.REQ_KEYFRAME, binding.REQ_STEP, binding.REQ_RENDER) == \
