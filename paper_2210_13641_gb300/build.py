@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False, ptxas
                 print(err)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [nvcc, ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, ARCH, "-shared", "-o", tmp, *objs, "-ldl"]  # -ldl: the NVTX v3 headers load a tool by dlopen
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/nerfmap.h"
 #include "internal.h"
 
@@ -259,7 +261,9 @@ int phase(map_scene* h, int ph, uint32_t n_launch, cudaStream_t s, F&& f) {
         cudaEventCreate(&b);
         cudaEventRecord(a, s);
     }
+    nvtxRangePushA(kPhaseName[ph]);  // named host range around the phase's launches (profilers)
     f();
+    nvtxRangePop();
     int rc = check_launch(h, kPhaseName[ph]);
     if (h->prof_on) {
         cudaEventRecord(b, s);
