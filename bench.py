@@ -573,7 +573,7 @@ def algorithmic_bytes(cfg, n_samples, n_params):
 # the digest of the files below must match.
 NCU_TRAFFIC = {
     "sources": ["k_field_tc.cu", "encoding.cuh", "common.cuh", "tc_ptx.cuh"],
-    "sha256": "2fdcfa9e252232e4e7a46e485cf6318b40485bb6948810ec216a95fe66d97b24",
+    "sha256": "8cda8a221f64f41166e3f746ed2e7eddc0dd1370d5121e3a37c1c0f22d75b571",
     "samples": 15869619,
     "field_fwd": 296292352 + 1241936896,
     "field_bwd": 1719506688 + 98251008,

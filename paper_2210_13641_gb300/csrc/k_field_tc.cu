@@ -438,8 +438,8 @@ __global__ void __launch_bounds__(128, 4) k_group_fwd_tc(const GroupItem* __rest
 // block is launched with 80 per thread (two blocks of 384 threads per SM), the
 // MLP group takes 136, the IO group 64 (its prefetched inputs are dead while it
 // scatters), the SC group 40 (the scatter alone needs no more without spilling):
-// 128 x 136 + 128 x 64 + 128 x 40 = 384 x 80.  The
-// groups hand tiles over through named barriers:
+// 128 x 136 + 128 x 64 + 128 x 40 = 384 x 80.  The groups hand tiles over through
+// named barriers:
 //   kBarIn      IO -> MLP        the tile's encodings (X0) and row data are in place
 //   kBarDfReady MLP -> IO, SC    the chain is done (X0 free) and dL/dfeat is in smem
 //   kBarDfFree  IO, SC -> MLP    both scatters of the tile are done (dL/dfeat read)
@@ -513,7 +513,6 @@ __device__ __forceinline__ void mask_epilogue(uint32_t trow, uint8_t* tile, int 
     }
 }
 
-
 }  // namespace
 
 // kPose: also writes, per sample, dL/dp (world position; IO group) and the
@@ -543,7 +542,7 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_field_bwd_tc(DevCfg c, const
     uint8_t* tH3 = tX3 + kT32;   // 128 x 64  (later G3)
     uint8_t* tH4 = tH3 + kT64;   // 128 x 64  (later G4)
     uint8_t* tG5 = tH4 + kT64;   // 128 x 16
-    uint8_t* sDf = tG5 + kT16;   // 128 rows x 32 FP32
+    uint8_t* sDf = tG5 + kT16;   // dL/dfeat: [16 levels][128 rows] float2
     float4* sRow = reinterpret_cast<float4*>(sDf + kDfBytes);  // [128][2]
     float4* sX = sRow + 2 * 128;                                // [2][128]: (x, valid) of tile k at k & 1
     const float2* sDf2 = reinterpret_cast<const float2*>(sDf);
